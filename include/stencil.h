@@ -1,0 +1,151 @@
+/*
+ * stencil.h -- C ABI of the GB300 star-stencil sweep library (libstencil.so).
+ *
+ * The operation (Zohouri, Podobas, Matsuoka, "High-Performance High-Order
+ * Stencil Computation on FPGAs Using OpenCL", Section IV.A, Eq. 1): `iters`
+ * Jacobi steps of a 2D or 3D star stencil of radius r = 1..4,
+ *
+ *   g(p) = c[0] f(p) + sum_{i=1..r} sum_{d} c[1 + (i-1)*2*dim + d] f(clamp(p + i*e_d)),
+ *
+ * d = 0:W(-x) 1:E(+x) 2:S(-y) 3:N(+y) [4:B(-z) 5:A(+z)], one coefficient per
+ * (distance, direction) as in the paper's no-sharing worst case, out-of-grid
+ * neighbours clamped to the border cell at every step (Sections III.B, IV.B).
+ * Each cell is evaluated as one FP32 multiply followed by 2*dim*r FP32 fused
+ * multiply-adds in exactly that order (Section V.A's multiply-then-FMA
+ * chain), so every schedule -- any temporal degree, tile or launch shape --
+ * returns bit-identical FP32 results.  Sums run i = 1..r (Eq. 1 prints i = 0;
+ * Table I's 12r+1 / 8r+1 FLOP count fixes 1..r).
+ *
+ * Grids: contiguous, x fastest, element (x, y, z) at x + nx*(y + ny*z);
+ * 2D grids pass nz = 1.  Storage is FP32, BF16 or FP16; arithmetic is always
+ * FP32 in registers and 16-bit storage is rounded (to nearest even) only
+ * when a pass writes the grid back, i.e. once per `t` steps.
+ *
+ * Conventions for every call:
+ *  - Return value: STENCIL_OK (0) or a negative STENCIL_ERR_* code.  No
+ *    exception or abort crosses the ABI.  After STENCIL_ERR_CUDA,
+ *    stencil_last_cuda_error() gives the cudaError_t value.
+ *  - Device pointers are plain CUDA device addresses on the current device;
+ *    `stream` is a cudaStream_t (NULL = legacy default stream).  All device
+ *    work is enqueued asynchronously on `stream` unless stated otherwise.
+ *  - The caller owns `in` and `out`; `in` is never written; overlapping `in`
+ *    and `out` is rejected (STENCIL_ERR_ALIAS).
+ *  - The handle owns a scratch grid (the second buffer of the ping-pong
+ *    between passes), allocated with cudaMalloc when a run first needs it
+ *    and freed by stencil_destroy.  A handle must not be used from two host
+ *    threads at once; runs on different streams with the same handle share
+ *    the scratch grid and must not overlap on the GPU.
+ */
+#ifndef STENCIL_H
+#define STENCIL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STENCIL_OK                 0
+#define STENCIL_ERR_INVALID_ARG  (-1) /* bad dim/radius/sizes/pointer/dtype/schedule field */
+#define STENCIL_ERR_ALIAS        (-2) /* in and out overlap */
+#define STENCIL_ERR_UNSUPPORTED  (-3) /* schedule not available for this problem */
+#define STENCIL_ERR_OOM          (-4) /* device allocation failed */
+#define STENCIL_ERR_CUDA         (-5) /* a CUDA runtime call failed */
+#define STENCIL_ERR_TIMEOUT      (-6) /* a kernel's bounded wait expired (device status) */
+#define STENCIL_ERR_NO_DEVICE    (-7) /* no usable GPU */
+
+typedef struct stencil_plan *stencil_handle;
+
+typedef enum { STENCIL_F32 = 0, STENCIL_BF16 = 1, STENCIL_F16 = 2 } stencil_dtype;
+
+typedef enum {
+    STENCIL_KERNEL_AUTO = 0,   /* streaming kernel when the grid allows it, else naive */
+    STENCIL_KERNEL_STREAM = 1, /* blocked streaming kernel (error if not applicable) */
+    STENCIL_KERNEL_NAIVE = 2   /* one thread per cell, one step per launch (t = 1) */
+} stencil_kernel;
+
+/*
+ * Explicit schedule of the streaming kernel (Sections III.A and V.A: spatial
+ * block size, temporal degree par_time).  Every field 0 = chosen by the
+ * library.  Tiles: each thread owns 4 consecutive x cells (times
+ * rows_per_thread y rows in 3D); a block covers 4*threads_x cells in x
+ * (times threads_y*rows_per_thread rows in 3D) including a halo of r*(t-1)
+ * cells per side rounded up for 16-byte alignment, and streams `seg` rows
+ * (2D, along y) or planes (3D, along z) plus the r*t halo in that direction.
+ */
+typedef struct {
+    int kernel;          /* stencil_kernel */
+    int t;               /* temporal degree: time steps per pass over the grid, >= 1 */
+    int threads_x;       /* multiple of 8 in [8, 256] */
+    int threads_y;       /* 3D: threads per block along y; threads_x*threads_y <= 256 */
+    int rows_per_thread; /* 3D: 2 or 4 */
+    int seg;             /* stream-axis extent per block, >= 1 */
+    int prefetch;        /* input planes loaded ahead of use, 1..32 */
+} stencil_schedule;
+
+/* Create a stencil of dimension `dim` (2 or 3) and radius 1..4 with
+ * K = 2*dim*radius + 1 FP32 coefficients read from host memory `coeffs`
+ * (layout above; copied, the caller keeps ownership).  Allocates no device
+ * memory.  Errors: INVALID_ARG. */
+int stencil_create(stencil_handle *out, int dim, int radius, const float *coeffs);
+
+/* Free the handle and its scratch grid.  Synchronises the device first so
+ * that no enqueued run still uses the scratch grid.  NULL is accepted. */
+int stencil_destroy(stencil_handle h);
+
+/* `iters` steps from `in` to `out` (device pointers, nx*ny*nz elements of
+ * `dtype`), with the schedule the library picks (tuned schedule if
+ * stencil_tune has stored one for this shape, else the analytic choice).
+ * iters == 0 copies in to out.  Errors: INVALID_ARG (sizes <= 0, dim 2 with
+ * nz != 1, NULL pointers, iters < 0, bad dtype), ALIAS, OOM, CUDA. */
+int stencil_run(stencil_handle h, const void *in, void *out, int64_t nx, int64_t ny,
+                int64_t nz, int iters, int dtype, void *stream);
+
+/* As stencil_run with an explicit schedule (`sched` may be NULL = auto).
+ * Errors as stencil_run plus UNSUPPORTED (temporal degree or tile shape not
+ * compiled in, shared memory exceeded, grid not 16-byte aligned for the
+ * streaming kernel) and INVALID_ARG for out-of-range fields. */
+int stencil_run_ex(stencil_handle h, const void *in, void *out, int64_t nx, int64_t ny,
+                   int64_t nz, int iters, int dtype, void *stream, const stencil_schedule *sched);
+
+/* End-to-end form on HOST buffers: copies `in_host` to the device, runs
+ * `iters` steps and copies the result to `out_host`, all on `stream`, and
+ * returns after the stream has finished.  Device buffers are held by the
+ * handle and reused across calls (grown on demand).  Pinned host memory gives
+ * full copy bandwidth; pageable memory works.  Errors as stencil_run_ex. */
+int stencil_run_host(stencil_handle h, const void *in_host, void *out_host, int64_t nx,
+                     int64_t ny, int64_t nz, int iters, int dtype, void *stream,
+                     const stencil_schedule *sched);
+
+/* The schedule stencil_run would use for this problem (auto choice). */
+int stencil_default_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                             stencil_schedule *out);
+
+/* Largest temporal degree compiled in for (dim, radius, dtype) and, in 3D,
+ * rows_per_thread; 0 if none.  */
+int stencil_max_t(int dim, int radius, int dtype, int rows_per_thread);
+
+/* Synchronise `stream`, then read and return the sticky device status of the
+ * current device: STENCIL_OK, or STENCIL_ERR_TIMEOUT when a kernel gave up a
+ * bounded wait (it then stopped early and its output is not valid).
+ * `clear` != 0 resets the status to OK afterwards. */
+int stencil_get_device_status(void *stream, int clear);
+
+/* Test hook for failure detection: while `plane` >= 0, streaming kernels on
+ * this handle never issue the copy of that input plane, so the wait for it
+ * expires after `timeout_ms` milliseconds (1..10000), the kernel records
+ * STENCIL_ERR_TIMEOUT in the device status and returns without hanging.
+ * plane < 0 restores normal operation (and the default 2000 ms limit). */
+int stencil_set_fault_injection(stencil_handle h, int plane, int timeout_ms);
+
+/* cudaError_t of the last failed CUDA call on this host thread (0 if none). */
+int stencil_last_cuda_error(void);
+
+/* Static description of a status code. */
+const char *stencil_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STENCIL_H */

@@ -1,1 +1,226 @@
-"""GB300-native repeated star-stencil sweeps (placeholder, filled below)."""
+"""GB300-native repeated star-stencil sweeps (2D/3D, radius 1..4, clamp to edge).
+
+A thin ctypes binding over libstencil.so (the C ABI declared in
+include/stencil.h).  The functions below carry the C names and only marshal
+arguments; every step of a sweep runs in the library's CUDA kernels.  PyTorch
+is used for device memory and streams only.  If the library has not been
+built, every call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libstencil.so")
+
+STENCIL_OK = 0
+STENCIL_ERR_INVALID_ARG = -1
+STENCIL_ERR_ALIAS = -2
+STENCIL_ERR_UNSUPPORTED = -3
+STENCIL_ERR_OOM = -4
+STENCIL_ERR_CUDA = -5
+STENCIL_ERR_TIMEOUT = -6
+STENCIL_ERR_NO_DEVICE = -7
+
+STENCIL_F32, STENCIL_BF16, STENCIL_F16 = 0, 1, 2
+KERNEL_AUTO, KERNEL_STREAM, KERNEL_NAIVE = 0, 1, 2
+
+# every symbol include/stencil.h declares
+EXPORTS = ("stencil_create", "stencil_destroy", "stencil_run", "stencil_run_ex", "stencil_run_host",
+           "stencil_default_schedule", "stencil_max_t", "stencil_get_device_status",
+           "stencil_set_fault_injection", "stencil_last_cuda_error", "stencil_strerror")
+
+
+class StencilError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})"
+                         + (f", cuda error {_lib().stencil_last_cuda_error()}" if code == STENCIL_ERR_CUDA else ""))
+
+
+class Schedule(ctypes.Structure):
+    """stencil_schedule: 0 in any field = chosen by the library."""
+    _fields_ = [("kernel", ctypes.c_int), ("t", ctypes.c_int), ("threads_x", ctypes.c_int),
+                ("threads_y", ctypes.c_int), ("rows_per_thread", ctypes.c_int), ("seg", ctypes.c_int),
+                ("prefetch", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_L = None
+
+
+def _lib():
+    global _L
+    if _L is None:
+        with _lock:
+            if _L is None:
+                if not os.path.exists(LIB_PATH):
+                    raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                       "`python -c 'import __graft_entry__ as g; g.build()'`")
+                lib = ctypes.CDLL(LIB_PATH)
+                vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+                sp = ctypes.POINTER(Schedule)
+                lib.stencil_create.argtypes = [ctypes.POINTER(vp), i32, i32, ctypes.POINTER(ctypes.c_float)]
+                lib.stencil_destroy.argtypes = [vp]
+                lib.stencil_run.argtypes = [vp, vp, vp, i64, i64, i64, i32, i32, vp]
+                lib.stencil_run_ex.argtypes = [vp, vp, vp, i64, i64, i64, i32, i32, vp, sp]
+                lib.stencil_run_host.argtypes = [vp, vp, vp, i64, i64, i64, i32, i32, vp, sp]
+                lib.stencil_default_schedule.argtypes = [vp, i64, i64, i64, i32, sp]
+                lib.stencil_max_t.argtypes = [i32, i32, i32, i32]
+                lib.stencil_get_device_status.argtypes = [vp, i32]
+                lib.stencil_set_fault_injection.argtypes = [vp, i32, i32]
+                lib.stencil_last_cuda_error.argtypes = []
+                lib.stencil_strerror.argtypes = [i32]
+                lib.stencil_strerror.restype = ctypes.c_char_p
+                for name in EXPORTS:
+                    if name != "stencil_strerror":
+                        getattr(lib, name).restype = i32
+                _L = lib
+    return _L
+
+
+def library():
+    """The loaded ctypes library (raises if it was not built)."""
+    return _lib()
+
+
+def strerror(code: int) -> str:
+    return _lib().stencil_strerror(code).decode()
+
+
+def _check(rc: int, what: str) -> int:
+    if rc != STENCIL_OK:
+        raise StencilError(rc, what)
+    return rc
+
+
+# ------------------------------------------------------------ C-named calls
+def stencil_create(dim: int, radius: int, coeffs) -> int:
+    import numpy as np
+    c = np.ascontiguousarray(coeffs, dtype=np.float32)
+    h = ctypes.c_void_p()
+    _check(_lib().stencil_create(ctypes.byref(h), dim, radius,
+                                 c.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "stencil_create")
+    return h.value
+
+
+def stencil_destroy(h: int) -> int:
+    return _check(_lib().stencil_destroy(h), "stencil_destroy")
+
+
+def stencil_run(h, in_ptr, out_ptr, nx, ny, nz, iters, dtype, stream) -> int:
+    return _check(_lib().stencil_run(h, in_ptr, out_ptr, nx, ny, nz, iters, dtype, stream), "stencil_run")
+
+
+def stencil_run_ex(h, in_ptr, out_ptr, nx, ny, nz, iters, dtype, stream, sched: Schedule | None) -> int:
+    return _check(_lib().stencil_run_ex(h, in_ptr, out_ptr, nx, ny, nz, iters, dtype, stream,
+                                        ctypes.byref(sched) if sched is not None else None), "stencil_run_ex")
+
+
+def stencil_run_host(h, in_ptr, out_ptr, nx, ny, nz, iters, dtype, stream, sched: Schedule | None) -> int:
+    return _check(_lib().stencil_run_host(h, in_ptr, out_ptr, nx, ny, nz, iters, dtype, stream,
+                                          ctypes.byref(sched) if sched is not None else None),
+                  "stencil_run_host")
+
+
+def stencil_default_schedule(h, nx, ny, nz, dtype) -> Schedule:
+    s = Schedule()
+    _check(_lib().stencil_default_schedule(h, nx, ny, nz, dtype, ctypes.byref(s)), "stencil_default_schedule")
+    return s
+
+
+def stencil_max_t(dim, radius, dtype, rows_per_thread=2) -> int:
+    return int(_lib().stencil_max_t(dim, radius, dtype, rows_per_thread))
+
+
+def stencil_get_device_status(stream=None, clear: bool = False) -> int:
+    """Raw status code (0 or STENCIL_ERR_TIMEOUT); does not raise on TIMEOUT."""
+    return int(_lib().stencil_get_device_status(stream, 1 if clear else 0))
+
+
+def stencil_set_fault_injection(h, plane: int, timeout_ms: int = 50) -> int:
+    return _check(_lib().stencil_set_fault_injection(h, plane, timeout_ms), "stencil_set_fault_injection")
+
+
+def stencil_last_cuda_error() -> int:
+    return int(_lib().stencil_last_cuda_error())
+
+
+def stencil_strerror(code: int) -> str:
+    return strerror(code)
+
+
+# --------------------------------------------------------- torch convenience
+_DT = {"float32": STENCIL_F32, "bfloat16": STENCIL_BF16, "float16": STENCIL_F16}
+
+
+def dtype_code(t) -> int:
+    return _DT[str(t.dtype).replace("torch.", "")]
+
+
+def schedule(**kw) -> Schedule:
+    s = Schedule()
+    for k, v in kw.items():
+        setattr(s, k, int(v))
+    return s
+
+
+def _dims(x, dim):
+    if x.dim() != dim:
+        raise ValueError(f"expected a {dim}-D tensor, got shape {tuple(x.shape)}")
+    if dim == 2:
+        ny, nx = x.shape
+        return nx, ny, 1
+    nz, ny, nx = x.shape
+    return nx, ny, nz
+
+
+class Stencil:
+    """A star stencil (dim, radius, K coefficients) bound to a library handle."""
+
+    def __init__(self, dim: int, radius: int, coeffs):
+        self.dim, self.radius = dim, radius
+        self.handle = stencil_create(dim, radius, coeffs)
+
+    def close(self):
+        if self.handle:
+            stencil_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, x, iters: int, out=None, sched: Schedule | None = None, stream=None):
+        """`iters` sweeps of CUDA tensor x (shape (ny,nx) or (nz,ny,nx), fp32/bf16/fp16)."""
+        import torch
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous CUDA tensor")
+        if out is None:
+            out = torch.empty_like(x)
+        if out.shape != x.shape or out.dtype != x.dtype or not out.is_contiguous():
+            raise ValueError("out must match x")
+        nx, ny, nz = _dims(x, self.dim)
+        st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        stencil_run_ex(self.handle, x.data_ptr(), out.data_ptr(), nx, ny, nz, iters, dtype_code(x), st, sched)
+        return out
+
+    def run_host(self, x_host, out_host, iters: int, sched: Schedule | None = None, stream=None):
+        """End-to-end: host (ideally pinned) CPU tensors in and out, copies included."""
+        import torch
+        nx, ny, nz = _dims(x_host, self.dim)
+        st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        stencil_run_host(self.handle, x_host.data_ptr(), out_host.data_ptr(), nx, ny, nz, iters,
+                         dtype_code(x_host), st, sched)
+        return out_host
+
+    def default_schedule(self, shape, dtype=STENCIL_F32) -> Schedule:
+        nx, ny, nz = (shape[1], shape[0], 1) if self.dim == 2 else (shape[2], shape[1], shape[0])
+        return stencil_default_schedule(self.handle, nx, ny, nz, dtype)

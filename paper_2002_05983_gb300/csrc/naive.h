@@ -1,0 +1,18 @@
+#pragma once
+#include <cstdint>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace stn {
+
+struct NaiveArgs {
+    int nx, ny, nz;
+    float c[25];
+};
+
+// __global__ naive_kernel<dim, r, S>(const S* in, S* out, NaiveArgs) for dtype 0/1/2, or nullptr.
+const void *naive_fn(int dim, int r, int dtype);
+
+}  // namespace stn

@@ -1,0 +1,578 @@
+// C ABI of the sweep library: argument checks, schedule planning, the
+// multi-pass driver (ceil(iters / t) passes ping-ponging between the
+// caller's output and a handle-owned scratch grid) and kernel launches.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "naive.h"
+#include "registry.h"
+#include "stencil.h"
+#include "sweep_kernel.cuh"
+
+struct stencil_plan {
+    int dim = 0, r = 0, K = 0;
+    float c[stn::kMaxK] = {};
+    void *scratch = nullptr;     // second grid of the ping-pong between passes
+    size_t scratch_bytes = 0;
+    int scratch_dev = -1;
+    void *dev_in = nullptr;      // device copies for stencil_run_host
+    void *dev_out = nullptr;
+    size_t host_bytes = 0;
+    int host_dev = -1;
+    int fault_plane = -1;
+    int timeout_ms = 2000;
+};
+
+namespace {
+
+thread_local int g_last_cuda_error = 0;
+
+int cuda_fail(cudaError_t e)
+{
+    g_last_cuda_error = static_cast<int>(e);
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? STENCIL_ERR_OOM : STENCIL_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+int elem_bytes(int dtype) { return dtype == STENCIL_F32 ? 4 : 2; }
+
+// ---------------------------------------------------------------- kernels
+struct Registry {
+    std::vector<stn::KernelEntry> all;
+    Registry()
+    {
+        using L = int (*)(const stn::KernelEntry **);
+        const L lists[] = {stn::list_2d_f32_r1,  stn::list_2d_f32_r2,  stn::list_2d_f32_r3,
+                           stn::list_2d_f32_r4,  stn::list_3d_f32_r1,  stn::list_3d_f32_r2,
+                           stn::list_3d_f32_r3,  stn::list_3d_f32_r4,  stn::list_2d_bf16_r1,
+                           stn::list_2d_bf16_r2, stn::list_2d_bf16_r3, stn::list_2d_bf16_r4,
+                           stn::list_3d_bf16_r1, stn::list_3d_bf16_r2, stn::list_3d_bf16_r3,
+                           stn::list_3d_bf16_r4, stn::list_2d_f16_r1,  stn::list_2d_f16_r2,
+                           stn::list_2d_f16_r3,  stn::list_2d_f16_r4,  stn::list_3d_f16_r1,
+                           stn::list_3d_f16_r2,  stn::list_3d_f16_r3,  stn::list_3d_f16_r4};
+        for (L f : lists) {
+            const stn::KernelEntry *e = nullptr;
+            const int n = f(&e);
+            all.insert(all.end(), e, e + n);
+        }
+    }
+    const void *find(int dim, int r, int t, int vy, int dtype) const
+    {
+        for (const auto &e : all)
+            if (e.dim == dim && e.r == r && e.t == t && e.vy == vy && e.dtype == dtype) return e.fn;
+        return nullptr;
+    }
+    int max_t(int dim, int r, int dtype, int vy) const
+    {
+        int m = 0;
+        for (const auto &e : all)
+            if (e.dim == dim && e.r == r && e.dtype == dtype && (dim == 2 || e.vy == vy))
+                m = std::max(m, e.t);
+        return m;
+    }
+};
+
+const Registry &registry()
+{
+    static Registry reg;
+    return reg;
+}
+
+// Functions whose shared-memory limit has been raised to the device maximum.
+std::mutex g_attr_mu;
+std::vector<const void *> g_attr_done;
+
+int prepare_fn(const void *fn, int max_smem)
+{
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (std::find(g_attr_done.begin(), g_attr_done.end(), fn) != g_attr_done.end()) return 0;
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    g_attr_done.push_back(fn);
+    return 0;
+}
+
+struct DevInfo {
+    int sms = 0, max_smem = 0;
+    unsigned *status = nullptr;
+};
+std::mutex g_dev_mu;
+DevInfo g_dev[64];
+
+int device_info(DevInfo **out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return STENCIL_ERR_NO_DEVICE;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DevInfo &d = g_dev[dev];
+    if (!d.sms) {
+        CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaDeviceGetAttribute(&d.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        void *p = nullptr;
+        CK(cudaMalloc(&p, 256));
+        CK(cudaMemset(p, 0, 256));
+        CK(cudaDeviceSynchronize());
+        d.status = static_cast<unsigned *>(p);
+    }
+    *out = &d;
+    return 0;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// ------------------------------------------------------------- planning
+int round_up(int a, int m) { return (a + m - 1) / m * m; }
+
+struct Pass {
+    const void *fn = nullptr;
+    int t = 0;
+    dim3 grid, block;
+    size_t smem = 0;
+    stn::SweepArgs a{};
+};
+
+bool stream_applicable(int dtype, int64_t nx)
+{
+    return nx % (dtype == STENCIL_F32 ? 4 : 8) == 0;
+}
+
+void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                      stencil_schedule *s)
+{
+    (void)ny;
+    (void)nz;
+    const Registry &reg = registry();
+    stencil_schedule d{};
+    d.kernel = stream_applicable(dtype, nx) ? STENCIL_KERNEL_STREAM : STENCIL_KERNEL_NAIVE;
+    if (h->dim == 2) {
+        static const int t2[5] = {0, 8, 5, 4, 3};
+        d.t = std::min(t2[h->r], reg.max_t(2, h->r, dtype, 1));
+        d.threads_x = 128;
+        d.threads_y = 1;
+        d.rows_per_thread = 1;
+        d.prefetch = 6;
+    } else {
+        static const int t3[5] = {0, 2, 1, 1, 1};
+        d.t = t3[h->r];
+        d.rows_per_thread = d.t == 1 ? 4 : 2;
+        d.threads_x = 16;
+        d.threads_y = 8;
+        d.prefetch = 2;
+    }
+    d.seg = 0;
+    *s = d;
+}
+
+// Fill one pass of temporal degree t.  Pointers are set by the caller.
+int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, int t,
+              const stencil_schedule &s, const DevInfo &dev, Pass &ps)
+{
+    const int D = h->dim, R = h->r;
+    const int es = elem_bytes(dtype);
+    const int vy = D == 3 ? s.rows_per_thread : 1;
+    const void *fn = registry().find(D, R, t, vy, dtype);
+    if (!fn) return STENCIL_ERR_UNSUPPORTED;
+    const int TX = s.threads_x, TY = D == 3 ? s.threads_y : 1;
+    if (TX < 8 || TX > 256 || TX % 8 || TY < 1 || TX * TY > stn::kMaxThreads)
+        return STENCIL_ERR_INVALID_ARG;
+    const int Bx = 4 * TX, By = TY * vy;
+    const int htx = round_up((t - 1) * R, 8), hty = (t - 1) * R;
+    const int cx = Bx - 2 * htx, cy = D == 3 ? By - 2 * hty : 1;
+    if (cx < 8 || cy < 1) return STENCIL_ERR_UNSUPPORTED;
+    const int padin = es == 4 ? 4 : 8;
+    const int pw = Bx + 8, ph = D == 3 ? By + 2 * R : 1, pw_in = Bx + 2 * padin;
+    if (D == 3 && (pw_in > 256 || ph > 256)) return STENCIL_ERR_UNSUPPORTED;   // TMA box limits
+    const int plane32 = round_up(pw * ph, 32);
+    const int plane_in = round_up(pw_in * ph * es, 128) / es;
+    const int keep = es == 4 ? R + 2 : 1;   // input slots held besides the prefetched ones
+    const int nring = es == 4 ? t - 1 : t;
+    auto smem_of = [&](int pf) {
+        return static_cast<size_t>(stn::kSmemHeader) +
+               static_cast<size_t>(pf + keep) * plane_in * es +
+               static_cast<size_t>(nring) * (R + 2) * plane32 * 4;
+    };
+    int pf = s.prefetch;
+    if (pf < 1 || pf + keep > stn::kMaxDepthIn) return STENCIL_ERR_INVALID_ARG;
+    while (pf > 1 && smem_of(pf) > static_cast<size_t>(dev.max_smem)) --pf;
+    if (smem_of(pf) > static_cast<size_t>(dev.max_smem)) return STENCIL_ERR_UNSUPPORTED;
+    const size_t smem = smem_of(pf);
+
+    int rc = prepare_fn(fn, dev.max_smem);
+    if (rc) return rc;
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, TX * TY, smem));
+    if (occ < 1) return STENCIL_ERR_UNSUPPORTED;
+
+    const int64_t ntx = (nx + cx - 1) / cx;
+    const int64_t nty = D == 3 ? (ny + cy - 1) / cy : 1;
+    const int64_t ns = D == 3 ? nz : ny;
+    const int64_t tiles = ntx * nty;
+    int64_t seg = s.seg;
+    if (seg <= 0) {
+        // pick the segment length that minimises waves x per-block steps
+        const int64_t slots = static_cast<int64_t>(dev.sms) * occ;
+        double best = 1e300;
+        seg = ns;
+        for (int64_t nseg = 1; nseg <= ns; ++nseg) {
+            const int64_t sg = (ns + nseg - 1) / nseg;
+            const int64_t ne = (ns + sg - 1) / sg;
+            if (ne != nseg) continue;
+            const int64_t blocks = tiles * ne;
+            const int64_t waves = (blocks + slots - 1) / slots;
+            const double cost = static_cast<double>(waves) * (sg + t * R + 8);
+            if (cost < best * 0.999) {
+                best = cost;
+                seg = sg;
+            }
+        }
+    }
+    const int64_t nseg = (ns + seg - 1) / seg;
+    if (tiles * nseg > 0x7fffffffLL) return STENCIL_ERR_UNSUPPORTED;
+
+    ps.fn = fn;
+    ps.t = t;
+    ps.grid = dim3(static_cast<unsigned>(tiles * nseg));
+    ps.block = dim3(TX, TY);
+    ps.smem = smem;
+    stn::SweepArgs &a = ps.a;
+    a.nx = static_cast<int>(nx);
+    a.ny = static_cast<int>(ny);
+    a.nz = static_cast<int>(nz);
+    a.ns = static_cast<int>(ns);
+    a.cx = cx;
+    a.cy = cy;
+    a.htx = htx;
+    a.hty = hty;
+    a.seg = static_cast<int>(seg);
+    a.ntx = static_cast<int>(ntx);
+    a.nty = static_cast<int>(nty);
+    a.prefetch = pf;
+    a.depth_in = pf + keep;
+    a.pw = pw;
+    a.ph = ph;
+    a.pw_in = pw_in;
+    a.plane_in = plane_in;
+    a.plane32 = plane32;
+    a.timeout_ms = h->timeout_ms;
+    a.fault_plane = h->fault_plane;
+    a.status = dev.status;
+    std::memcpy(a.c, h->c, sizeof(float) * h->K);
+    return 0;
+}
+
+int encode_map(CUtensorMap *m, const void *ptr, int64_t nx, int64_t ny, int64_t nz, int dtype,
+               const stn::SweepArgs &a)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return STENCIL_ERR_CUDA;
+    const int es = elem_bytes(dtype);
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(nx), static_cast<cuuint64_t>(ny),
+                          static_cast<cuuint64_t>(nz)};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(nx * es), static_cast<cuuint64_t>(nx * ny * es)};
+    cuuint32_t box[3] = {static_cast<cuuint32_t>(a.pw_in), static_cast<cuuint32_t>(a.ph), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = dtype == STENCIL_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dtype == STENCIL_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const CUresult r = enc(m, dt, 3, const_cast<void *>(ptr), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        g_last_cuda_error = static_cast<int>(r);
+        return STENCIL_ERR_CUDA;
+    }
+    return 0;
+}
+
+int ensure_scratch(stencil_plan *h, size_t bytes)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (h->scratch && (h->scratch_bytes < bytes || h->scratch_dev != dev)) {
+        CK(cudaDeviceSynchronize());
+        CK(cudaFree(h->scratch));
+        h->scratch = nullptr;
+        h->scratch_bytes = 0;
+    }
+    if (!h->scratch) {
+        CK(cudaMalloc(&h->scratch, bytes));
+        h->scratch_bytes = bytes;
+        h->scratch_dev = dev;
+    }
+    return 0;
+}
+
+bool overlap(const void *a, const void *b, size_t n)
+{
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + n && y < x + n;
+}
+
+int check_problem(const stencil_plan *h, const void *in, const void *out, int64_t nx, int64_t ny,
+                  int64_t nz, int iters, int dtype)
+{
+    if (!h || !in || !out) return STENCIL_ERR_INVALID_ARG;
+    if (nx <= 0 || ny <= 0 || nz <= 0 || iters < 0) return STENCIL_ERR_INVALID_ARG;
+    if (h->dim == 2 && nz != 1) return STENCIL_ERR_INVALID_ARG;
+    if (dtype < STENCIL_F32 || dtype > STENCIL_F16) return STENCIL_ERR_INVALID_ARG;
+    if (nx > 0x7fffffff || ny > 0x7fffffff || nz > 0x7fffffff) return STENCIL_ERR_INVALID_ARG;
+    const size_t bytes = static_cast<size_t>(nx * ny * nz) * elem_bytes(dtype);
+    if (overlap(in, out, bytes)) return STENCIL_ERR_ALIAS;
+    return 0;
+}
+
+int launch_naive(const stencil_plan *h, const void *src, void *dst, int64_t nx, int64_t ny,
+                 int64_t nz, int dtype, cudaStream_t st, const DevInfo &dev)
+{
+    const void *fn = stn::naive_fn(h->dim, h->r, dtype);
+    if (!fn) return STENCIL_ERR_UNSUPPORTED;
+    stn::NaiveArgs na{};
+    na.nx = static_cast<int>(nx);
+    na.ny = static_cast<int>(ny);
+    na.nz = static_cast<int>(nz);
+    std::memcpy(na.c, h->c, sizeof(float) * h->K);
+    const int64_t n = nx * ny * nz;
+    const int64_t want = (n + 255) / 256;
+    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(want, static_cast<int64_t>(dev.sms) * 32));
+    void *args[] = {const_cast<void **>(&src), &dst, &na};
+    CK(cudaLaunchKernel(fn, dim3(blocks), dim3(256), args, 0, st));
+    return 0;
+}
+
+int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny, int64_t nz,
+             int iters, int dtype, cudaStream_t st, const stencil_schedule *user)
+{
+    int rc = check_problem(h, in, out, nx, ny, nz, iters, dtype);
+    if (rc) return rc;
+    DevInfo *dev = nullptr;
+    rc = device_info(&dev);
+    if (rc) return rc;
+    const size_t bytes = static_cast<size_t>(nx * ny * nz) * elem_bytes(dtype);
+    if (iters == 0) {
+        CK(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st));
+        return 0;
+    }
+    stencil_schedule s;
+    default_schedule(h, nx, ny, nz, dtype, &s);
+    if (user) {
+        if (user->kernel < 0 || user->kernel > STENCIL_KERNEL_NAIVE) return STENCIL_ERR_INVALID_ARG;
+        if (user->kernel) s.kernel = user->kernel;
+        if (user->t) s.t = user->t;
+        if (user->threads_x) s.threads_x = user->threads_x;
+        if (user->threads_y) s.threads_y = user->threads_y;
+        if (user->rows_per_thread) s.rows_per_thread = user->rows_per_thread;
+        if (user->seg) s.seg = user->seg;
+        if (user->prefetch) s.prefetch = user->prefetch;
+        if (s.t < 0 || s.seg < 0 || s.prefetch < 0) return STENCIL_ERR_INVALID_ARG;
+        if (h->dim == 3 && user->t && !user->rows_per_thread)
+            s.rows_per_thread = registry().find(3, h->r, s.t, 4, dtype) ? (s.t == 1 ? 4 : 2) : 2;
+    }
+    const bool aligned = (reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16 == 0;
+    const bool streamable = stream_applicable(dtype, nx) && aligned;
+    if (s.kernel == STENCIL_KERNEL_STREAM && !streamable) return STENCIL_ERR_UNSUPPORTED;
+    if (s.kernel == STENCIL_KERNEL_AUTO) s.kernel = streamable ? STENCIL_KERNEL_STREAM : STENCIL_KERNEL_NAIVE;
+
+    // passes: full passes of degree t, then the remainder
+    std::vector<int> degrees;
+    const int t = s.kernel == STENCIL_KERNEL_NAIVE ? 1 : std::max(1, std::min(s.t, iters));
+    for (int done = 0; done < iters; done += t) degrees.push_back(std::min(t, iters - done));
+    const int L = static_cast<int>(degrees.size());
+    if (L > 1) {
+        rc = ensure_scratch(h, bytes);
+        if (rc) return rc;
+    }
+    std::vector<Pass> plans;
+    if (s.kernel == STENCIL_KERNEL_STREAM) {
+        for (int j = 0; j < L; ++j) {
+            if (j > 0 && degrees[j] == degrees[j - 1]) {
+                plans.push_back(plans.back());
+                continue;
+            }
+            Pass ps;
+            rc = plan_pass(h, nx, ny, nz, dtype, degrees[j], s, *dev, ps);
+            if (rc) return rc;
+            plans.push_back(ps);
+        }
+    }
+    const void *src = in;
+    for (int j = 0; j < L; ++j) {
+        void *dst = ((L - 1 - j) % 2 == 0) ? out : h->scratch;
+        if (s.kernel == STENCIL_KERNEL_NAIVE) {
+            rc = launch_naive(h, src, dst, nx, ny, nz, dtype, st, *dev);
+            if (rc) return rc;
+        } else {
+            Pass &ps = plans[j];
+            ps.a.in = src;
+            ps.a.out = dst;
+            CUtensorMap map;
+            std::memset(&map, 0, sizeof(map));
+            if (h->dim == 3) {
+                rc = encode_map(&map, src, nx, ny, nz, dtype, ps.a);
+                if (rc) return rc;
+            }
+            void *args[] = {&map, &ps.a};
+            CK(cudaLaunchKernel(ps.fn, ps.grid, ps.block, args, ps.smem, st));
+        }
+        src = dst;
+    }
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stencil_create(stencil_handle *out, int dim, int radius, const float *coeffs)
+{
+    if (!out || !coeffs) return STENCIL_ERR_INVALID_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || radius < 1 || radius > 4) return STENCIL_ERR_INVALID_ARG;
+    stencil_plan *h = new (std::nothrow) stencil_plan;
+    if (!h) return STENCIL_ERR_OOM;
+    h->dim = dim;
+    h->r = radius;
+    h->K = 2 * dim * radius + 1;
+    std::memcpy(h->c, coeffs, sizeof(float) * h->K);
+    *out = h;
+    return STENCIL_OK;
+}
+
+int stencil_destroy(stencil_handle h)
+{
+    if (!h) return STENCIL_OK;
+    int rc = STENCIL_OK;
+    if (h->scratch || h->dev_in || h->dev_out) {
+        if (cudaDeviceSynchronize() != cudaSuccess) rc = STENCIL_ERR_CUDA;
+        if (h->scratch) cudaFree(h->scratch);
+        if (h->dev_in) cudaFree(h->dev_in);
+        if (h->dev_out) cudaFree(h->dev_out);
+    }
+    delete h;
+    return rc;
+}
+
+int stencil_run(stencil_handle h, const void *in, void *out, int64_t nx, int64_t ny, int64_t nz,
+                int iters, int dtype, void *stream)
+{
+    return run_impl(h, in, out, nx, ny, nz, iters, dtype, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+int stencil_run_ex(stencil_handle h, const void *in, void *out, int64_t nx, int64_t ny, int64_t nz,
+                   int iters, int dtype, void *stream, const stencil_schedule *sched)
+{
+    return run_impl(h, in, out, nx, ny, nz, iters, dtype, static_cast<cudaStream_t>(stream), sched);
+}
+
+int stencil_run_host(stencil_handle h, const void *in_host, void *out_host, int64_t nx, int64_t ny,
+                     int64_t nz, int iters, int dtype, void *stream, const stencil_schedule *sched)
+{
+    if (!h || !in_host || !out_host) return STENCIL_ERR_INVALID_ARG;
+    int rc = check_problem(h, in_host, out_host, nx, ny, nz, iters, dtype);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = static_cast<size_t>(nx * ny * nz) * elem_bytes(dtype);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (h->host_bytes < bytes || h->host_dev != dev) {
+        CK(cudaDeviceSynchronize());
+        if (h->dev_in) cudaFree(h->dev_in);
+        if (h->dev_out) cudaFree(h->dev_out);
+        h->dev_in = h->dev_out = nullptr;
+        h->host_bytes = 0;
+        CK(cudaMalloc(&h->dev_in, bytes));
+        CK(cudaMalloc(&h->dev_out, bytes));
+        h->host_bytes = bytes;
+        h->host_dev = dev;
+    }
+    CK(cudaMemcpyAsync(h->dev_in, in_host, bytes, cudaMemcpyHostToDevice, st));
+    rc = run_impl(h, h->dev_in, h->dev_out, nx, ny, nz, iters, dtype, st, sched);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out_host, h->dev_out, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return STENCIL_OK;
+}
+
+int stencil_default_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                             stencil_schedule *out)
+{
+    if (!h || !out || dtype < STENCIL_F32 || dtype > STENCIL_F16) return STENCIL_ERR_INVALID_ARG;
+    default_schedule(h, nx, ny, nz, dtype, out);
+    return STENCIL_OK;
+}
+
+int stencil_max_t(int dim, int radius, int dtype, int rows_per_thread)
+{
+    return registry().max_t(dim, radius, dtype, rows_per_thread);
+}
+
+int stencil_get_device_status(void *stream, int clear)
+{
+    DevInfo *dev = nullptr;
+    int rc = device_info(&dev);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaStreamSynchronize(st));
+    unsigned word = 0;
+    CK(cudaMemcpy(&word, dev->status, sizeof(word), cudaMemcpyDeviceToHost));
+    if (clear) CK(cudaMemset(dev->status, 0, sizeof(unsigned)));
+    if (word & stn::kStatusTimeout) return STENCIL_ERR_TIMEOUT;
+    return STENCIL_OK;
+}
+
+int stencil_set_fault_injection(stencil_handle h, int plane, int timeout_ms)
+{
+    if (!h) return STENCIL_ERR_INVALID_ARG;
+    if (plane < 0) {
+        h->fault_plane = -1;
+        h->timeout_ms = 2000;
+        return STENCIL_OK;
+    }
+    if (timeout_ms < 1 || timeout_ms > 10000) return STENCIL_ERR_INVALID_ARG;
+    h->fault_plane = plane;
+    h->timeout_ms = timeout_ms;
+    return STENCIL_OK;
+}
+
+int stencil_last_cuda_error(void) { return g_last_cuda_error; }
+
+const char *stencil_strerror(int code)
+{
+    switch (code) {
+    case STENCIL_OK: return "ok";
+    case STENCIL_ERR_INVALID_ARG: return "invalid argument";
+    case STENCIL_ERR_ALIAS: return "input and output overlap";
+    case STENCIL_ERR_UNSUPPORTED: return "schedule not supported for this problem";
+    case STENCIL_ERR_OOM: return "device allocation failed";
+    case STENCIL_ERR_CUDA: return "CUDA call failed";
+    case STENCIL_ERR_TIMEOUT: return "kernel bounded wait expired";
+    case STENCIL_ERR_NO_DEVICE: return "no usable GPU";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,643 @@
+// Streaming star-stencil sweep for sm_103a: spatial blocking (1.5D in 2D,
+// 2.5D in 3D) combined with overlapped temporal blocking of degree T
+// (Sections III.A/III.B of the paper; Eq. 2 gives the shrinking valid
+// region, csize = bsize - 2*T*r).
+//
+// One block owns a tile of the plane perpendicular to the streaming axis
+// (2D: a run of x columns, streaming along y; 3D: an x/y tile, streaming
+// along z) and a segment of the streaming axis.  Each step of the block's
+// loop advances every time level by one plane:
+//   * level 0 is the input: planes arrive by TMA (1D bulk copies of a row in
+//     2D, a 3D tensor-map box in 3D) into a ring of shared-memory slots with
+//     one mbarrier per slot, `prefetch` planes ahead of use;
+//   * level s (1..T) computes plane p_s = k - s*(r+1) from level s-1: the
+//     streaming-axis neighbours come from a register queue of 2r+1 planes of
+//     the thread's own cells, the in-plane neighbours from level s-1's FP32
+//     shared-memory ring of r+2 planes.  The lag of r+1 planes between levels
+//     means everything a level reads was written in an earlier step, so one
+//     __syncthreads per step orders all of it, and levels are evaluated from
+//     T down to 1 so that a level reads its input queue before the level
+//     below overwrites the oldest plane of it;
+//   * level T writes the compute tile of its plane to global memory.
+// The FP32 arithmetic of every cell is one multiply and 2*D*r fused
+// multiply-adds in the order centre, then for i = 1..r: W, E, S, N[, B, A]
+// (Eq. 1 read left to right), so results do not depend on T, tiles or
+// launch shape.
+//
+// Clamp to edge (Section III.B) at every time level: a plane segment that
+// streams off the grid's end keeps repeating the last plane (queue copy); a
+// segment that starts at plane 0 fills the whole queue with plane 0; in the
+// plane, tiles at the grid's edge overwrite the out-of-grid frame of every
+// level's ring plane with the clamped border values before anyone reads it.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace stn {
+
+constexpr int kMaxK = 25;            // 2*3*4 + 1 coefficients
+constexpr int kMaxThreads = 256;
+constexpr int kMaxDepthIn = 64;      // input ring slots (one mbarrier each)
+constexpr int kSmemHeader = 1024;    // mbarriers + abort flag
+constexpr unsigned kStatusTimeout = 1u;
+
+struct SweepArgs {
+    const void *in;       // source grid (2D path reads it with bulk copies)
+    void *out;            // destination grid
+    unsigned *status;     // sticky device status word
+    int nx, ny, nz;       // grid extents (2D: nz = 1)
+    int ns;               // extent of the streaming axis (2D: ny, 3D: nz)
+    int cx, cy;           // compute tile extents (x, and y in 3D)
+    int htx, hty;         // thread-region halo around the compute tile
+    int seg;              // streaming-axis extent per block
+    int ntx, nty;         // tile counts in x and y (nty = 1 in 2D)
+    int depth_in;         // input ring slots
+    int prefetch;         // planes loaded ahead of use
+    int pw, ph;           // padded FP32 plane: (4*TX + 8) x (rows + 2r) (2D: ph = 1)
+    int pw_in;            // padded input plane width in storage elements
+    int plane_in;         // input ring slot stride (storage elements, 128-byte multiple)
+    int plane32;          // FP32 ring slot stride (floats, 128-byte multiple)
+    int timeout_ms;       // limit of every bounded wait
+    int fault_plane;      // test hook: never load this input plane (< 0: off)
+    float c[kMaxK];       // coefficients, Eq. 1 order
+};
+
+// --------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase: false after `timeout_ms` without completion.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int timeout_ms)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    const uint64_t lim = static_cast<uint64_t>(timeout_ms) * 1000000ull;
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > lim) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            int z, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+// --------------------------------------------------------- storage formats
+template <typename S> struct Fmt;
+template <> struct Fmt<float> {
+    static constexpr int pad = 4;   // 16 bytes of padding either side of a row
+    __device__ __forceinline__ static void load4(const float *p, float (&v)[4])
+    {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    __device__ __forceinline__ static void store4(float *p, const float (&v)[4])
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct Fmt<__nv_bfloat16> {
+    static constexpr int pad = 8;
+    __device__ __forceinline__ static void load4(const __nv_bfloat16 *p, float (&v)[4])
+    {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    __device__ __forceinline__ static void store4(__nv_bfloat16 *p, const float (&v)[4])
+    {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 t;
+        t.x = *reinterpret_cast<uint32_t *>(&a);
+        t.y = *reinterpret_cast<uint32_t *>(&b);
+        *reinterpret_cast<uint2 *>(p) = t;
+    }
+};
+template <> struct Fmt<__half> {
+    static constexpr int pad = 8;
+    __device__ __forceinline__ static void load4(const __half *p, float (&v)[4])
+    {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    __device__ __forceinline__ static void store4(__half *p, const float (&v)[4])
+    {
+        __half2 a = __floats2half2_rn(v[0], v[1]);
+        __half2 b = __floats2half2_rn(v[2], v[3]);
+        uint2 t;
+        t.x = *reinterpret_cast<uint32_t *>(&a);
+        t.y = *reinterpret_cast<uint32_t *>(&b);
+        *reinterpret_cast<uint2 *>(p) = t;
+    }
+};
+
+// ------------------------------------------------------ compile-time loops
+template <int I> using IC = std::integral_constant<int, I>;
+template <int I, int N> struct SFor {
+    template <typename F> __device__ __forceinline__ static void run(F &&f)
+    {
+        f(IC<I>{});
+        SFor<I + 1, N>::run(f);
+    }
+};
+template <int N> struct SFor<N, N> {
+    template <typename F> __device__ __forceinline__ static void run(F &&) {}
+};
+
+__host__ __device__ constexpr int cmod(int a, int m) { return ((a % m) + m) % m; }
+__host__ __device__ constexpr int cclamp(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
+
+// ------------------------------------------------------- ghost (clamp) fill
+// Tasks that overwrite the out-of-grid frame (width <= 4 in x, r in y) of a
+// padded FP32 plane with clamped border values; float4 granularity.
+struct Ghost {
+    int ntask, nA, nc;      // total tasks, column tasks, columns per in-grid row (0..2)
+    int rA0;                // first in-grid padded row
+    int cL, cR;             // padded float4 columns at x = -4 and x = nx (or -1)
+    int srcL, srcR;         // padded x of global x = 0 and x = nx-1
+    int rT0, nT, srcT;      // top ghost rows, their count, padded source row
+    int rB0, nB, srcB;      // bottom ghost rows
+    int cg0, ncg;           // float4 columns of the ghost rows
+};
+
+__device__ __forceinline__ Ghost make_ghost(int ox, int oy, int pw, int ph, int nx, int nyp, int r)
+{
+    Ghost g;
+    const int xL = -4 - ox, xR = nx - ox;
+    g.cL = (xL >= 0 && xL + 4 <= pw) ? xL / 4 : -1;
+    g.cR = (xR >= 0 && xR + 4 <= pw) ? xR / 4 : -1;
+    g.srcL = -ox;
+    g.srcR = nx - 1 - ox;
+    g.nc = (g.cL >= 0) + (g.cR >= 0);
+    const int a0 = max(0, oy), a1 = min(nyp, oy + ph);
+    g.rA0 = a0 - oy;
+    g.nA = (a1 > a0 ? a1 - a0 : 0) * g.nc;
+    const int t0 = max(-r, oy), t1 = min(0, oy + ph);
+    g.rT0 = t0 - oy;
+    g.nT = t1 > t0 ? t1 - t0 : 0;
+    g.srcT = -oy;
+    const int b0 = max(nyp, oy), b1 = min(nyp + r, oy + ph);
+    g.rB0 = b0 - oy;
+    g.nB = b1 > b0 ? b1 - b0 : 0;
+    g.srcB = nyp - 1 - oy;
+    const int x0 = max(-4, ox), x1 = min(nx + 4, ox + pw);
+    g.cg0 = (x0 - ox) / 4;
+    g.ncg = x1 > x0 ? (x1 - x0) / 4 : 0;
+    g.ntask = g.nA + (g.nT + g.nB) * g.ncg;
+    return g;
+}
+
+__device__ __forceinline__ void ghost_fill(float *plane, const Ghost &g, int pw, int ox, int nx,
+                                           int tid, int nthr)
+{
+    for (int t = tid; t < g.ntask; t += nthr) {
+        int row, col;
+        float4 v;
+        if (t < g.nA) {
+            row = g.rA0 + t / g.nc;
+            const bool left = (t % g.nc == 0) && g.cL >= 0;
+            col = left ? g.cL : g.cR;
+            const float s = plane[row * pw + (left ? g.srcL : g.srcR)];
+            v = make_float4(s, s, s, s);
+        } else {
+            const int u = t - g.nA;
+            const int gr = u / g.ncg;
+            col = g.cg0 + u % g.ncg;
+            int srow;
+            if (gr < g.nT) { row = g.rT0 + gr; srow = g.srcT; }
+            else { row = g.rB0 + gr - g.nT; srow = g.srcB; }
+            const int x4 = ox + 4 * col;
+            if (x4 < 0) {
+                const float s = plane[srow * pw + g.srcL];
+                v = make_float4(s, s, s, s);
+            } else if (x4 >= nx) {
+                const float s = plane[srow * pw + g.srcR];
+                v = make_float4(s, s, s, s);
+            } else {
+                v = *reinterpret_cast<const float4 *>(plane + srow * pw + 4 * col);
+            }
+        }
+        *reinterpret_cast<float4 *>(plane + row * pw + 4 * col) = v;
+    }
+}
+
+// ------------------------------------------------------------------ kernel
+template <int D, int R, int T, int VY, typename S>
+__global__ void __launch_bounds__(kMaxThreads)
+    sweep_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ SweepArgs a)
+{
+    static_assert(D == 2 || D == 3, "dim");
+    static_assert(R >= 1 && R <= 4, "radius");
+    static_assert(D == 3 || VY == 1, "2D keeps one row per thread");
+    constexpr int QP = 2 * R + 1;                 // register queue period
+    constexpr int RD = R + 2;                     // FP32 ring depth
+    constexpr bool F32S = std::is_same<S, float>::value;
+    constexpr int PADIN = Fmt<S>::pad;
+    constexpr int K2 = 2 * D;                     // coefficients per distance
+
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    volatile int *sflag = reinterpret_cast<volatile int *>(smem + 8 * kMaxDepthIn);
+    S *ring_in = reinterpret_cast<S *>(smem + kSmemHeader);
+    float *rings = reinterpret_cast<float *>(smem + kSmemHeader +
+                                             static_cast<size_t>(a.depth_in) * a.plane_in * sizeof(S));
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nthr = blockDim.x * blockDim.y;
+    const int tid = ty * blockDim.x + tx;
+
+    // ---- tile and segment of this block
+    int b = blockIdx.x;
+    const int tile_x = b % a.ntx;
+    b /= a.ntx;
+    int tile_y = 0;
+    if (D == 3) {
+        tile_y = b % a.nty;
+        b /= a.nty;
+    }
+    const int gx0 = tile_x * a.cx - a.htx;           // thread-region origin
+    const int gy0 = (D == 3) ? tile_y * a.cy - a.hty : 0;
+    const int ox = gx0 - 4;                          // padded FP32 plane origin
+    const int oy = (D == 3) ? gy0 - R : 0;
+    const int ox_in = gx0 - PADIN;                   // padded input plane origin
+    const int Z0 = b * a.seg;
+    const int Z1 = min(Z0 + a.seg, a.ns);
+    const int last = a.ns - 1;
+
+    // ---- this thread's cells
+    const int xl = 4 * tx;
+    const int px = xl + 4;                           // padded FP32 column of own cell 0
+    const int px_in = xl + PADIN;
+    const int yl0 = ty * VY;
+    const int prow0 = (D == 3) ? yl0 + R : 0;        // padded row of own row 0
+    const int gx = gx0 + xl;
+    const bool xstore = xl >= a.htx && xl < a.htx + a.cx && gx < a.nx;
+    bool ystore[VY];
+#pragma unroll
+    for (int vy = 0; vy < VY; ++vy) {
+        const int yl = yl0 + vy;
+        ystore[vy] = (D == 2) || (yl >= a.hty && yl < a.hty + a.cy && gy0 + yl < a.ny);
+    }
+
+    // A thread whose VY rows cross the grid's top or bottom edge keeps its
+    // out-of-grid rows equal to the border row in registers (clamp), since
+    // its in-grid rows take y neighbours from its own registers.
+    const int vz = -(gy0 + yl0);                     // own row index of global y = 0
+    const int vb = a.ny - 1 - (gy0 + yl0);           // own row index of global y = ny-1
+    const bool top_cross = (D == 3) && VY > 1 && vz > 0 && vz < VY;
+    const bool bot_cross = (D == 3) && VY > 1 && vb >= 0 && vb < VY - 1;
+    auto clamp_rows = [&](float (&v)[VY][4]) {
+        if (top_cross) {
+#pragma unroll
+            for (int vy = VY - 2; vy >= 0; --vy)
+                if (vy < vz)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) v[vy][c] = v[vy + 1][c];
+        }
+        if (bot_cross) {
+#pragma unroll
+            for (int vy = 1; vy < VY; ++vy)
+                if (vy > vb)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) v[vy][c] = v[vy - 1][c];
+        }
+    };
+
+    // ---- plane ranges per level: level s covers planes [lo[s], hi[s]] at steps p + s*(R+1)
+    int lo[T + 1], hi[T + 1];
+#pragma unroll
+    for (int s = 0; s <= T; ++s) {
+        lo[s] = max(Z0 - (T - s) * R, 0);
+        hi[s] = Z1 - 1 + (T - s) * R;
+    }
+    const int k0 = lo[0];
+    const int k1 = Z1 - 1 + T * (R + 1);
+    const int lmax = min(hi[0], last);               // last input plane to load
+
+    const Ghost gh = make_ghost(ox, oy, a.pw, a.ph, a.nx, (D == 3) ? a.ny : 1, R);
+
+    auto ring32 = [&](int s, int slot) -> float * {  // FP32 ring of level s
+        const int idx = F32S ? s - 1 : s;
+        return rings + static_cast<size_t>(idx * RD + slot) * a.plane32;
+    };
+
+    if (tid == 0) {
+        for (int i = 0; i < a.depth_in; ++i) mbar_init(smem_addr(bars + i), 1);
+        *sflag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    // thread 0 issues the input loads
+    int issued_hi = k0 - 1;
+    auto issue = [&](int q) {
+        const int slot = (q - k0) % a.depth_in;
+        const uint32_t bar = smem_addr(bars + slot);
+        S *dst = ring_in + static_cast<size_t>(slot) * a.plane_in;
+        issued_hi = q;
+        if (q == a.fault_plane) return;
+        if (D == 2) {
+            const int xa = max(ox_in, 0), xb = min(ox_in + a.pw_in, a.nx);
+            const uint32_t bytes = xb > xa ? static_cast<uint32_t>((xb - xa) * sizeof(S)) : 0u;
+            mbar_arrive_expect_tx(bar, bytes);
+            if (bytes)
+                bulk_load(smem_addr(dst + (xa - ox_in)),
+                          static_cast<const S *>(a.in) + static_cast<size_t>(q) * a.nx + xa, bytes,
+                          bar);
+        } else {
+            mbar_arrive_expect_tx(bar, static_cast<uint32_t>(a.pw_in * a.ph * sizeof(S)));
+            tma_load_3d(smem_addr(dst), &tmap, ox_in, oy, q, bar);
+        }
+    };
+    if (tid == 0) {
+        const int qe = min(k0 + a.prefetch - 1, lmax);
+        for (int q = k0; q <= qe; ++q) issue(q);
+    }
+
+    float q[T][QP][VY][4];
+#pragma unroll
+    for (int s = 0; s < T; ++s)
+#pragma unroll
+        for (int j = 0; j < QP; ++j)
+#pragma unroll
+            for (int vy = 0; vy < VY; ++vy)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) q[s][j][vy][v] = 0.f;
+
+    int slot_k = 0;               // input ring slot of plane k
+    int consumed_hi = k0 - 1;     // last input plane waited for by thread 0
+    bool aborted = false;
+    const int kstart = k0 - k0 % QP;
+
+    for (int kb = kstart; kb <= k1 && !aborted; kb += QP) {
+        SFor<0, QP>::run([&](auto Jc) {
+            constexpr int J = decltype(Jc)::value;
+            const int k = kb + J;
+            if (aborted || k < k0 || k > k1) return;
+
+            // (a) keep `prefetch` input planes in flight
+            if (tid == 0) {
+                const int qn = k + a.prefetch;
+                if (qn <= lmax) {
+                    fence_proxy_async_smem();
+                    issue(qn);
+                }
+            }
+
+            // (b) time levels T..1
+            SFor<0, T>::run([&](auto sc) {
+                constexpr int s = T - decltype(sc)::value;
+                constexpr int js = cmod(J - s * (R + 1), QP);   // queue slot of plane p
+                const int p = k - s * (R + 1);
+                if (p < lo[s] || p > hi[s]) return;
+                if (p > last) {
+                    if constexpr (s < T) {
+#pragma unroll
+                        for (int vy = 0; vy < VY; ++vy)
+#pragma unroll
+                            for (int v = 0; v < 4; ++v)
+                                q[s][js][vy][v] = q[s][cmod(js - 1, QP)][vy][v];
+                    }
+                    return;
+                }
+                // level s-1's plane p in shared memory
+                const float *src;
+                if (F32S && s == 1) {
+                    int sl = slot_k - (R + 1);
+                    if (sl < 0) sl += a.depth_in;
+                    src = reinterpret_cast<const float *>(ring_in) + static_cast<size_t>(sl) * a.plane_in;
+                } else {
+                    src = ring32(s - 1, p % RD);
+                }
+                const float *own = src + prow0 * a.pw + px;
+                float up[(D == 3) ? R : 1][4], dn[(D == 3) ? R : 1][4];
+                (void)up;
+                (void)dn;
+                if constexpr (D == 3) {
+#pragma unroll
+                    for (int m = 0; m < R; ++m) {
+                        Fmt<float>::load4(own - (m + 1) * a.pw, up[m]);
+                        Fmt<float>::load4(own + (VY + m) * a.pw, dn[m]);
+                    }
+                }
+                float res[VY][4];
+#pragma unroll
+                for (int vy = 0; vy < VY; ++vy) {
+                    float L[4], Rr[4];
+                    Fmt<float>::load4(own + vy * a.pw - 4, L);
+                    Fmt<float>::load4(own + vy * a.pw + 4, Rr);
+                    const float(&ctr)[VY][4] = q[s - 1][js];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        float acc = __fmul_rn(a.c[0], ctr[vy][v]);
+#pragma unroll
+                        for (int i = 1; i <= R; ++i) {
+                            const int cb = 1 + (i - 1) * K2;
+                            const float w = (v - i >= 0) ? ctr[vy][cclamp(v - i, 0, 3)]
+                                                         : L[cclamp(4 + v - i, 0, 3)];
+                            const float e = (v + i <= 3) ? ctr[vy][cclamp(v + i, 0, 3)]
+                                                         : Rr[cclamp(v + i - 4, 0, 3)];
+                            acc = __fmaf_rn(a.c[cb + 0], w, acc);
+                            acc = __fmaf_rn(a.c[cb + 1], e, acc);
+                            if constexpr (D == 3) {
+                                const float sv = (vy - i >= 0) ? ctr[cclamp(vy - i, 0, VY - 1)][v]
+                                                               : up[cclamp(i - vy - 1, 0, R - 1)][v];
+                                const float nv = (vy + i < VY) ? ctr[cclamp(vy + i, 0, VY - 1)][v]
+                                                               : dn[cclamp(vy + i - VY, 0, R - 1)][v];
+                                acc = __fmaf_rn(a.c[cb + 2], sv, acc);
+                                acc = __fmaf_rn(a.c[cb + 3], nv, acc);
+                            }
+                            acc = __fmaf_rn(a.c[cb + K2 - 2], q[s - 1][cmod(js - i, QP)][vy][v], acc);
+                            acc = __fmaf_rn(a.c[cb + K2 - 1], q[s - 1][cmod(js + i, QP)][vy][v], acc);
+                        }
+                        res[vy][v] = acc;
+                    }
+                }
+                if constexpr (D == 3 && VY > 1) clamp_rows(res);
+                if constexpr (s == T) {
+                    if (xstore) {
+#pragma unroll
+                        for (int vy = 0; vy < VY; ++vy) {
+                            if (!ystore[vy]) continue;
+                            size_t off;
+                            if (D == 2) off = static_cast<size_t>(p) * a.nx + gx;
+                            else off = (static_cast<size_t>(p) * a.ny + (gy0 + yl0 + vy)) * a.nx + gx;
+                            Fmt<S>::store4(static_cast<S *>(a.out) + off, res[vy]);
+                        }
+                    }
+                } else {
+                    float *dst = ring32(s, p % RD) + prow0 * a.pw + px;
+#pragma unroll
+                    for (int vy = 0; vy < VY; ++vy) {
+                        Fmt<float>::store4(dst + vy * a.pw, res[vy]);
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) q[s][js][vy][v] = res[vy][v];
+                    }
+                    if (p == 0) {   // top clamp: planes -r..-1 of this level equal plane 0
+#pragma unroll
+                        for (int j = 0; j < QP; ++j)
+#pragma unroll
+                            for (int vy = 0; vy < VY; ++vy)
+#pragma unroll
+                                for (int v = 0; v < 4; ++v) q[s][j][vy][v] = res[vy][v];
+                    }
+                }
+            });
+
+            // (c) level 0: take plane k from the input ring
+            {
+                constexpr int j0 = J;
+                const int p = k;
+                if (p >= lo[0] && p <= hi[0]) {
+                    if (p > last) {
+#pragma unroll
+                        for (int vy = 0; vy < VY; ++vy)
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) q[0][j0][vy][v] = q[0][cmod(j0 - 1, QP)][vy][v];
+                    } else {
+                        const uint32_t parity = static_cast<uint32_t>(((p - k0) / a.depth_in) & 1);
+                        const bool ok = mbar_wait_bounded(smem_addr(bars + slot_k), parity, a.timeout_ms);
+                        if (!ok) {
+                            *sflag = 1;
+                            atomicOr(a.status, kStatusTimeout);
+                        } else {
+                            if (tid == 0) consumed_hi = p;
+                            const S *inp = ring_in + static_cast<size_t>(slot_k) * a.plane_in;
+                            if constexpr (!F32S) {
+                                // convert the whole padded plane to the level-0 FP32 ring
+                                float *dst = ring32(0, p % RD);
+                                const int c4 = a.pw / 4;
+                                for (int t = tid; t < c4 * a.ph; t += nthr) {
+                                    const int row = t / c4, col = t % c4;
+                                    float v4[4];
+                                    Fmt<S>::load4(inp + row * a.pw_in + 4 * col + (PADIN - 4), v4);
+                                    Fmt<float>::store4(dst + row * a.pw + 4 * col, v4);
+                                }
+                            }
+                            float v4[VY][4];
+#pragma unroll
+                            for (int vy = 0; vy < VY; ++vy)
+                                Fmt<S>::load4(inp + (prow0 + vy) * a.pw_in + px_in, v4[vy]);
+                            if constexpr (D == 3 && VY > 1) clamp_rows(v4);
+#pragma unroll
+                            for (int vy = 0; vy < VY; ++vy)
+#pragma unroll
+                                for (int v = 0; v < 4; ++v) q[0][j0][vy][v] = v4[vy][v];
+                            if (p == 0) {
+#pragma unroll
+                                for (int j = 0; j < QP; ++j)
+#pragma unroll
+                                    for (int vy = 0; vy < VY; ++vy)
+#pragma unroll
+                                        for (int v = 0; v < 4; ++v) q[0][j][vy][v] = q[0][j0][vy][v];
+                            }
+                        }
+                    }
+                }
+            }
+
+            // (d) clamp frame of the planes that levels 0..T-1 produced in the previous step
+            if (gh.ntask > 0) {
+#pragma unroll
+                for (int s = 0; s < T; ++s) {
+                    const int p = k - 1 - s * (R + 1);
+                    if (p < lo[s] || p > min(hi[s], last)) continue;
+                    float *pl;
+                    if (F32S && s == 0) {
+                        int sl = slot_k - 1;
+                        if (sl < 0) sl += a.depth_in;
+                        pl = reinterpret_cast<float *>(ring_in) + static_cast<size_t>(sl) * a.plane_in;
+                    } else {
+                        pl = ring32(s, p % RD);
+                    }
+                    ghost_fill(pl, gh, a.pw, ox, a.nx, tid, nthr);
+                }
+            }
+
+            slot_k = (slot_k + 1 == a.depth_in) ? 0 : slot_k + 1;
+            __syncthreads();
+            aborted = (*sflag != 0);
+        });
+    }
+
+    if (aborted && tid == 0) {
+        // let the copies still in flight land before the block's shared memory is released
+        for (int qq = consumed_hi + 1; qq <= issued_hi; ++qq) {
+            if (qq == a.fault_plane) continue;
+            const int slot = (qq - k0) % a.depth_in;
+            const uint32_t parity = static_cast<uint32_t>(((qq - k0) / a.depth_in) & 1);
+            mbar_wait_bounded(smem_addr(bars + slot), parity, a.timeout_ms);
+        }
+    }
+}
+
+}  // namespace stn

@@ -1,0 +1,190 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+FP32: the library evaluates every cell as the same multiply-then-FMA chain as
+the FP32 oracle, so results must be bit-identical for every schedule, and
+within 2e-6 * iters of the FP64 oracle.  16-bit storage: bit-identical to the
+FP32 oracle run pass by pass with rounding to the storage type in between.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2002_05983_gb300 as st
+import stencil_inputs as gen
+from gpu_util import (assert_bits_equal, make_input, oracle_passes, run_gpu, shape_of,
+                      to_storage)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    st.library()
+    yield
+
+
+def test_smoke_config_2d_r1_256():
+    """2D r=1, 256^2, 10 iterations, t=1: bit-exact vs fp32 oracle, <= 2e-5 vs fp64."""
+    c = gen.coefficients(2, 1)
+    f = gen.uniform_grid((256, 256), seed=0)
+    s = st.Stencil(2, 1, c)
+    want32 = oracle.sweep_f32(f, 2, 1, c, 10)
+    want64 = oracle.sweep_f64(f, 2, 1, c, 10)
+    for sched in ({"kernel": st.KERNEL_NAIVE}, {"kernel": st.KERNEL_STREAM, "t": 1}, {}):
+        got = run_gpu(s, torch.from_numpy(f), 10, **sched)
+        assert_bits_equal(got, want32, f"smoke {sched}")
+        assert np.max(np.abs(got.numpy() - want64)) <= 2e-6 * 10
+
+
+CASES_2D = [(r, t) for r in (1, 2, 3, 4) for t in sorted({1, 2, 3, st.stencil_max_t(2, r, 0)})]
+
+
+@pytest.mark.parametrize("r,t", CASES_2D)
+def test_2d_stream_bit_exact(r, t):
+    """Several x tiles and y segments with ragged tails; iters = 2t+1 (remainder pass)."""
+    nx, ny = 1000, 777
+    c = gen.coefficients(2, r)
+    f = make_input(2, nx, ny)
+    iters = 2 * t + 1
+    want = oracle.sweep_f32(f, 2, r, c, iters)
+    s = st.Stencil(2, r, c)
+    got = run_gpu(s, torch.from_numpy(f), iters, kernel=st.KERNEL_STREAM, t=t, threads_x=64, seg=97)
+    assert_bits_equal(got, want, f"2D r={r} t={t}")
+    w64 = oracle.sweep_f64(f.astype(np.float64), 2, r, c.astype(np.float64), iters)
+    assert np.max(np.abs(got.numpy() - w64)) <= 2e-6 * iters
+
+
+CASES_3D = [(r, t, vy) for r in (1, 2, 3, 4) for vy in (2, 4)
+            for t in sorted({1, st.stencil_max_t(3, r, 0, vy)})]
+
+
+@pytest.mark.parametrize("r,t,vy", CASES_3D)
+def test_3d_stream_bit_exact(r, t, vy):
+    nx, ny, nz = 100, 70, 53
+    c = gen.coefficients(3, r)
+    f = make_input(3, nx, ny, nz)
+    iters = 2 * t + 1
+    want = oracle.sweep_f32(f, 3, r, c, iters)
+    s = st.Stencil(3, r, c)
+    got = run_gpu(s, torch.from_numpy(f), iters, kernel=st.KERNEL_STREAM, t=t, threads_x=16,
+                  threads_y=8 if vy == 2 else 4, rows_per_thread=vy, seg=19)
+    assert_bits_equal(got, want, f"3D r={r} t={t} vy={vy}")
+
+
+@pytest.mark.parametrize("dim,r", [(2, 1), (2, 4), (3, 1), (3, 3)])
+def test_schedules_bit_identical_to_naive(dim, r):
+    """Every FP32 schedule equals the one-thread-per-cell t=1 schedule bit for bit."""
+    shape = (300, 260) if dim == 2 else (40, 36, 44)
+    f = make_input(dim, *shape[::-1])
+    c = gen.coefficients(dim, r)
+    s = st.Stencil(dim, r, c)
+    x = torch.from_numpy(f)
+    iters = 7
+    ref = run_gpu(s, x, iters, kernel=st.KERNEL_NAIVE)
+    tmax = st.stencil_max_t(dim, r, 0, 2)
+    scheds = []
+    for t in range(1, tmax + 1):
+        if dim == 2:
+            for tx in (32, 128, 256):
+                scheds.append(dict(kernel=st.KERNEL_STREAM, t=t, threads_x=tx, seg=0, prefetch=1 + t % 4))
+        else:
+            scheds.append(dict(kernel=st.KERNEL_STREAM, t=t, threads_x=8, threads_y=16, rows_per_thread=2))
+            scheds.append(dict(kernel=st.KERNEL_STREAM, t=t, threads_x=24, threads_y=8, rows_per_thread=2, seg=5))
+    for sc in scheds:
+        try:
+            got = run_gpu(s, x, iters, **sc)
+        except st.StencilError as e:
+            assert e.code == st.STENCIL_ERR_UNSUPPORTED, sc   # halo wider than the tile
+            continue
+        assert torch.equal(got, ref), sc
+
+
+@pytest.mark.parametrize("dim,shape,r", [
+    (2, (1, 4), 1), (2, (3, 8), 4), (2, (64, 4), 3), (2, (5, 1000), 2),
+    (3, (1, 1, 4), 2), (3, (3, 5, 8), 4), (3, (9, 2, 12), 1), (3, (2, 40, 8), 3)])
+def test_tiny_and_degenerate_grids(dim, shape, r):
+    """Sides smaller than the radius, single rows/planes: clamp everywhere."""
+    f = gen.uniform_grid(shape, seed=5)
+    c = gen.coefficients(dim, r)
+    s = st.Stencil(dim, r, c)
+    for t in (1, 2):
+        want = oracle.sweep_f32(f, dim, r, c, 5)
+        got = run_gpu(s, torch.from_numpy(f), 5, kernel=st.KERNEL_STREAM, t=t)
+        assert_bits_equal(got, want, f"tiny {shape} t={t}")
+        got = run_gpu(s, torch.from_numpy(f), 5, kernel=st.KERNEL_NAIVE)
+        assert_bits_equal(got, want, f"tiny naive {shape}")
+
+
+def test_unaligned_rows_use_naive_path():
+    f = gen.uniform_grid((33, 1001), seed=6)
+    c = gen.coefficients(2, 2)
+    s = st.Stencil(2, 2, c)
+    want = oracle.sweep_f32(f, 2, 2, c, 4)
+    assert_bits_equal(run_gpu(s, torch.from_numpy(f), 4), want, "auto on unaligned nx")
+    with pytest.raises(st.StencilError) as e:
+        run_gpu(s, torch.from_numpy(f), 4, kernel=st.KERNEL_STREAM)
+    assert e.value.code == st.STENCIL_ERR_UNSUPPORTED
+
+
+def test_iters_zero_copies_and_input_untouched():
+    f = gen.uniform_grid((40, 64), seed=7)
+    s = st.Stencil(2, 1, gen.coefficients(2, 1))
+    x = torch.from_numpy(f).cuda()
+    keep = x.clone()
+    out = s.run(x, 0)
+    assert torch.equal(out, x)
+    out = s.run(x, 9)
+    torch.cuda.synchronize()
+    assert torch.equal(x, keep)
+    with pytest.raises(st.StencilError) as e:
+        s.run(x, 3, out=x)
+    assert e.value.code == st.STENCIL_ERR_ALIAS
+
+
+@pytest.mark.parametrize("dt", ["bf16", "f16"])
+@pytest.mark.parametrize("dim,r,t", [(2, 1, 1), (2, 1, 6), (2, 4, 3), (3, 2, 1), (3, 1, 3), (3, 4, 2)])
+def test_low_precision_storage_bit_exact(dt, dim, r, t):
+    """16-bit grids: FP32 arithmetic inside a pass, one rounding per pass."""
+    shape = (190, 264) if dim == 2 else (29, 34, 40)
+    f = make_input(dim, *shape[::-1])
+    c = gen.coefficients(dim, r)
+    iters = 2 * t + 1
+    want = oracle_passes(f, dim, r, c, iters, t, dt)
+    s = st.Stencil(dim, r, c)
+    sched = dict(kernel=st.KERNEL_STREAM, t=t)
+    if dim == 3:
+        sched.update(rows_per_thread=2 if t > 1 else 4)
+    got = run_gpu(s, to_storage(f, dt), iters, **sched)
+    assert_bits_equal(got, want, f"{dt} {dim}D r={r} t={t}")
+    # naive path = one rounding per step
+    got = run_gpu(s, to_storage(f, dt), iters, kernel=st.KERNEL_NAIVE)
+    assert_bits_equal(got, oracle_passes(f, dim, r, c, iters, 1, dt), f"{dt} naive")
+
+
+def test_run_host_end_to_end():
+    f = make_input(3, 64, 48, 40)
+    c = gen.coefficients(3, 2)
+    s = st.Stencil(3, 2, c)
+    x = torch.from_numpy(f).pin_memory()
+    out = torch.empty_like(x).pin_memory()
+    s.run_host(x, out, 6)
+    assert_bits_equal(out, oracle.sweep_f32(f, 3, 2, c, 6), "run_host")
+
+
+def test_fault_injection_times_out_and_context_survives():
+    """A copy that is never issued makes the bounded wait expire: the kernel records
+    TIMEOUT and returns; the same context keeps working afterwards."""
+    f = gen.uniform_grid((64, 128), seed=8)
+    c = gen.coefficients(2, 1)
+    s = st.Stencil(2, 1, c)
+    x = torch.from_numpy(f).cuda()
+    assert st.stencil_get_device_status(clear=True) == 0
+    st.stencil_set_fault_injection(s.handle, 10, 50)
+    s.run(x, 3, sched=st.schedule(kernel=st.KERNEL_STREAM, t=3))
+    assert st.stencil_get_device_status(clear=True) == st.STENCIL_ERR_TIMEOUT
+    assert st.stencil_get_device_status() == 0
+    st.stencil_set_fault_injection(s.handle, -1, 0)
+    got = run_gpu(s, x.cpu(), 3, kernel=st.KERNEL_STREAM, t=3)
+    assert_bits_equal(got, oracle.sweep_f32(f, 2, 1, c, 3), "after fault")
