@@ -1,0 +1,366 @@
+"""Benchmark: repeated 2D star-stencil sweeps, radius 1..4, 16384 x 16384 FP32 grid,
+1000 iterations per radius, clamp to edge, each radius at the library's chosen
+temporal degree.  One "step" = the four radii back to back (4 x 1000 sweeps of
+the 1 GiB grid).  Metric: GCell/s = cells * iterations / time (Section IV.C,
+Eq. 3 of the paper), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain C sweep, OpenMP over the
+host cores) on a bounded crop of the same workload; it is the baseline the
+GPU path is compared with, and the only other place this file runs the oracle
+is the cpu_baseline field of the GPU line.
+Under torchrun (N > 1) every rank sweeps its own grids (independent problems,
+weak scaling, no collective on the data path); the barrier and a max-reduce
+of the elapsed time use the process group.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import stencil_inputs as gen  # noqa: E402
+
+METRIC = "GCell/s & GFLOP/s per radius (2D/3D), plain FP32 vs tuned/BF16, % of roofline"
+NX = NY = 16384
+ITERS = 1000
+RADII = (1, 2, 3, 4)
+WORKLOAD = "2D star stencils r=1..4, 16384x16384 FP32, 1000 iterations each, clamp to edge"
+SAMPLE_SIDE = 2048          # oracle sample: top-left 2048x2048 crop of the same input
+SAMPLE_ITERS = 100
+FALLBACK_HBM_GBS = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def crop_input(side: int) -> np.ndarray:
+    """Top-left side x side crop of the seeded 16384^2 input (same counters)."""
+    out = np.empty((side, side), np.float32)
+    for y in range(side):
+        gen.uniform(gen.GRID_SEED, side, offset=y * NX, out=out[y])
+    return out
+
+
+def peaks():
+    p = {"hbm_gbs": FALLBACK_HBM_GBS, "hbm_src": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            m = json.load(fh)
+        if m.get("hbm_gbs"):
+            p = {"hbm_gbs": float(m["hbm_gbs"]), "hbm_src": "measured"}
+    from paper_2002_05983_gb300 import metrics
+    p["fp32_flops"] = metrics.FP32_PEAK_NOMINAL
+    return p
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], None, set()
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for(dim, r, t, dtype="f32"):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    src = os.path.join(ROOT, "paper_2002_05983_gb300", "csrc", "sweep_kernel.cuh")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for ln in open(path):
+        f = ln.split()
+        if len(f) == 6 and not ln.startswith("#") and f[0] == h and f[1:5] == [str(dim), str(r), str(t), dtype]:
+            return int(f[5])
+    return None
+
+
+def oracle_leg(steps: int, warmup: int):
+    """Time the CPU oracle on the crop; returns (GCell/s, seconds per step, cores, sample text)."""
+    import oracle
+    oracle.build()
+    f = crop_input(SAMPLE_SIDE)
+    coeffs = {r: gen.coefficients(2, r) for r in RADII}
+    cores = oracle.max_threads()
+
+    def one():
+        for r in RADII:
+            oracle.sweep_f32(f, 2, r, coeffs[r], SAMPLE_ITERS)
+
+    for _ in range(warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    dt = (time.perf_counter() - t0) / steps
+    cells = SAMPLE_SIDE * SAMPLE_SIDE * SAMPLE_ITERS * len(RADII)
+    sample = (f"oracle_sweep_f32 on the top-left {SAMPLE_SIDE}x{SAMPLE_SIDE} crop of the same input, "
+              f"r=1..4, {SAMPLE_ITERS} iterations each")
+    return cells / dt / 1e9, dt, cores, sample
+
+
+def reference_main(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    g, dt, cores, sample = oracle_leg(args.steps, args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": round(g, 4), "unit": "GCell/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": round(g, 4), "unit": "GCell/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(g, 4), "unit": "GCell/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def case_main(args):
+    """One radius on an n^dim grid: the small case used for ncu captures."""
+    import torch
+    import paper_2002_05983_gb300 as st
+    f = args.case.split(":")
+    dim, r, t, n, iters = (int(v) for v in f[:5])
+    dt = f[5] if len(f) > 5 else "f32"
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dt]
+    shape = (n, n) if dim == 2 else (n, n, n)
+    x = torch.from_numpy(gen.workload_grid(dim, *shape[::-1])).to(tdt).cuda()
+    out = torch.empty_like(x)
+    s = st.Stencil(dim, r, gen.coefficients(dim, r))
+    sched = st.schedule(kernel=st.KERNEL_STREAM, t=t) if t else None
+    for _ in range(args.warmup):
+        s.run(x, iters, out=out, sched=sched)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        s.run(x, iters, out=out, sched=sched)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3 / args.steps
+    assert st.stencil_get_device_status() == 0
+    print(json.dumps({"case": args.case, "gcells": round(x.numel() * iters / sec / 1e9, 2),
+                      "ms": round(sec * 1e3, 3)}), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None,
+                    help="single sweep for profiling: dim:r:t:n:iters[:dtype] (grid n^dim, t=0 auto)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_main(args)
+    if args.case:
+        return case_main(args)
+
+    import torch
+    import paper_2002_05983_gb300 as st
+    from paper_2002_05983_gb300 import metrics
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- inputs (seeded; 1 GiB, larger than L2 so no flush is needed between steps)
+    t0 = time.time()
+    host = torch.empty((NY, NX), dtype=torch.float32).pin_memory()
+    gen.uniform_grid((NY, NX), out=host.numpy())
+    x = host.cuda()
+    out = torch.empty_like(x)
+    host_out = torch.empty_like(host).pin_memory()
+    log(f"rank {rank}: input ready in {time.time() - t0:.1f}s")
+
+    stencils = {r: st.Stencil(2, r, gen.coefficients(2, r)) for r in RADII}
+    scheds = {r: stencils[r].default_schedule((NY, NX)) for r in RADII}
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        for r in RADII:
+            if ev is not None:
+                ev[r][0].record(stream)
+            stencils[r].run(x, ITERS, out=out)
+            if ev is not None:
+                ev[r][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    assert st.stencil_get_device_status() == 0
+
+    evs = [{r: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for r in RADII}
+           for _ in range(args.steps)]
+    e_start, e_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with Clocks(local) as clk:
+        e_start.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        e_stop.record(stream)
+        barrier()
+    elapsed = e_start.elapsed_time(e_stop) / 1e3
+    if st.stencil_get_device_status() != 0:
+        raise RuntimeError("device status reports a timed-out kernel")
+    if dist:
+        tt = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+
+    per_r = {}
+    for r in RADII:
+        per_r[r] = sum(evs[k][r][0].elapsed_time(evs[k][r][1]) for k in range(args.steps)) / 1e3 / args.steps
+    cells_step = NX * NY * ITERS * len(RADII)
+    value = cells_step * args.steps * world / elapsed / 1e9
+    flops_step = sum(NX * NY * ITERS * metrics.flop_per_cell(2, r) for r in RADII)
+
+    # ---- end to end through the C ABI on pinned host buffers (copies inside the timed region)
+    e2e_steps = max(1, args.steps // 2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for r in RADII:
+            stencils[r].run_host(host, host_out, ITERS)
+    barrier()
+    e2e_el = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([e2e_el], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_el = float(tt.item())
+    e2e = {"value": round(cells_step * e2e_steps * world / e2e_el / 1e9, 3), "unit": "GCell/s",
+           "h2d_bytes_per_step": host.numel() * 4 * len(RADII),
+           "d2h_bytes_per_step": host_out.numel() * 4 * len(RADII)}
+
+    # ---- roofline of the dominant kernel (the radius with the longest time)
+    pk = peaks()
+    rows = []
+    launches = 0
+    for r in RADII:
+        t = scheds[r].t
+        nl = -(-ITERS // t)
+        launches += nl * args.steps
+        sec = per_r[r]
+        g = NX * NY * ITERS / sec / 1e9
+        roof = metrics.roofline_cells(2, r, t, 4, pk["fp32_flops"], pk["hbm_gbs"] * 1e9) / 1e9
+        rows.append({"r": r, "t": t, "threads_x": scheds[r].threads_x, "gcells": round(g, 2),
+                     "gflops": round(g * metrics.flop_per_cell(2, r), 1),
+                     "roofline_gcells": round(roof, 1), "roofline_frac": round(g / roof, 4),
+                     "bound": metrics.roofline_bound(2, r, t, 4, pk["fp32_flops"], pk["hbm_gbs"] * 1e9),
+                     "ms": round(sec * 1e3, 2)})
+    dom = max(rows, key=lambda d: d["ms"])
+    nl = -(-ITERS // dom["t"])
+    launch_s = dom["ms"] / 1e3 / nl
+    if dom["bound"] == "hbm":
+        ach = NX * NY * 8 / launch_s / 1e9
+        roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "peak_source": pk["hbm_src"] + " copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        ach = NX * NY * dom["t"] * metrics.flop_per_cell(2, dom["r"]) / launch_s / 1e12
+        roofline = {"bound": "alu", "achieved": round(ach, 2), "peak": round(pk["fp32_flops"] / 1e12, 2),
+                    "unit": "TFLOP/s",
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (nominal)"}
+    roofline["frac"] = round(roofline["achieved"] / roofline["peak"], 4)
+    roofline["kernel"] = f"sweep_kernel<2D, r={dom['r']}, t={dom['t']}, fp32>"
+    roofline["traffic"] = traffic_for(2, dom["r"], dom["t"])
+    roofline["algorithmic_bytes_per_launch"] = NX * NY * 8
+
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "GCell/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [NY, NX], "iters": ITERS, "radii": list(RADII),
+                       "input": "uniform [0,1) from seed 0 (SplitMix64), coefficients seed 1",
+                       "l2": "inputs larger than L2 (1 GiB grid), no flush",
+                       "parallelism": f"replicas x{world}"},
+            "gflops": round(flops_step * args.steps * world / elapsed / 1e9, 1),
+            "per_radius": rows, "roofline": roofline, "e2e": e2e, "gpu_launches": launches}
+    clk = clk.summary()
+    if clk:
+        line["clocks"] = clk
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        g, dt, cores, sample = oracle_leg(1, 0)
+        line["cpu_baseline"] = {"value": round(g, 4), "unit": "GCell/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -67,20 +67,22 @@ typedef enum {
 /*
  * Explicit schedule of the streaming kernel (Sections III.A and V.A: spatial
  * block size, temporal degree par_time).  Every field 0 = chosen by the
- * library.  Tiles: each thread owns 4 consecutive x cells (times
- * rows_per_thread y rows in 3D); a block covers 4*threads_x cells in x
- * (times threads_y*rows_per_thread rows in 3D) including a halo of r*(t-1)
- * cells per side rounded up for 16-byte alignment, and streams `seg` rows
- * (2D, along y) or planes (3D, along z) plus the r*t halo in that direction.
+ * library.  Blocks have a compiled shape: 2D 128 threads, each owning 4
+ * consecutive x cells (a 512-cell row strip streamed along y); 3D 16 x 8
+ * threads, each owning 4 x cells times rows_per_thread y rows (a 64-cell
+ * wide tile streamed along z).  The strip/tile includes a halo of r*(t-1)
+ * cells per side (x halo rounded up to 8) recomputed by neighbouring blocks
+ * (overlapped blocking, Eq. 2), and each block streams `seg` rows/planes
+ * plus r*t halo planes of the stream axis.
  */
 typedef struct {
     int kernel;          /* stencil_kernel */
     int t;               /* temporal degree: time steps per pass over the grid, >= 1 */
-    int threads_x;       /* multiple of 8 in [8, 256] */
-    int threads_y;       /* 3D: threads per block along y; threads_x*threads_y <= 256 */
+    int threads_x;       /* 0, or the compiled block width (2D 128, 3D 16) */
+    int threads_y;       /* 0, or the compiled block height (3D 8) */
     int rows_per_thread; /* 3D: 2 or 4 */
     int seg;             /* stream-axis extent per block, >= 1 */
-    int prefetch;        /* input planes loaded ahead of use, 1..32 */
+    int prefetch;        /* 0, or the compiled number of planes loaded ahead */
 } stencil_schedule;
 
 /* Create a stencil of dimension `dim` (2 or 3) and radius 1..4 with

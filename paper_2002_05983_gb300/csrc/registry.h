@@ -1,11 +1,18 @@
 // Table of compiled streaming-kernel instantiations (filled by sweep*_*.cu).
 #pragma once
+#include <cstddef>
+
+#include "sweep_cfg.h"
 
 namespace stn {
 
 struct KernelEntry {
     int dim, r, t, vy, dtype;   // dtype: 0 fp32, 1 bf16, 2 fp16
-    const void *fn;             // __global__ sweep_kernel<dim, r, t, vy, S>
+    int tx, ty;                 // block shape
+    int cx, cy, htx, hty;       // compute tile and thread-region halo
+    int pf;                     // planes loaded ahead of use
+    size_t smem;                // dynamic shared memory bytes
+    const void *fn;             // __global__ sweep_kernel<dim, r, t, vy, S, tx, ty>
 };
 
 int list_2d_f32_r1(const KernelEntry **e);
@@ -35,4 +42,9 @@ int list_3d_f16_r4(const KernelEntry **e);
 
 }  // namespace stn
 
-#define STN_E(D, R, T, VY, S, DT) {D, R, T, VY, DT, reinterpret_cast<const void *>(&stn::sweep_kernel<D, R, T, VY, S>)}
+#define STN_G(D, R, T, VY, S, TX, TY) stn::Geo<D, R, T, VY, static_cast<int>(sizeof(S)), TX, TY>
+#define STN_E(D, R, T, VY, S, DT, TX, TY)                                                          \
+    {D, R, T, VY, DT, TX, TY, STN_G(D, R, T, VY, S, TX, TY)::CX, STN_G(D, R, T, VY, S, TX, TY)::CY, \
+     STN_G(D, R, T, VY, S, TX, TY)::HTX, STN_G(D, R, T, VY, S, TX, TY)::HTY,                        \
+     STN_G(D, R, T, VY, S, TX, TY)::PF, STN_G(D, R, T, VY, S, TX, TY)::SMEM,                        \
+     reinterpret_cast<const void *>(&stn::sweep_kernel<D, R, T, VY, S, TX, TY>)}

@@ -68,10 +68,10 @@ struct Registry {
             all.insert(all.end(), e, e + n);
         }
     }
-    const void *find(int dim, int r, int t, int vy, int dtype) const
+    const stn::KernelEntry *find(int dim, int r, int t, int vy, int dtype) const
     {
         for (const auto &e : all)
-            if (e.dim == dim && e.r == r && e.t == t && e.vy == vy && e.dtype == dtype) return e.fn;
+            if (e.dim == dim && e.r == r && e.t == t && (dim == 2 || e.vy == vy) && e.dtype == dtype) return &e;
         return nullptr;
     }
     int max_t(int dim, int r, int dtype, int vy) const
@@ -170,21 +170,19 @@ void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz,
     stencil_schedule d{};
     d.kernel = stream_applicable(dtype, nx) ? STENCIL_KERNEL_STREAM : STENCIL_KERNEL_NAIVE;
     if (h->dim == 2) {
-        static const int t2[5] = {0, 8, 5, 4, 3};
+        static const int t2[5] = {0, 6, 4, 2, 2};
         d.t = std::min(t2[h->r], reg.max_t(2, h->r, dtype, 1));
         d.threads_x = 128;
         d.threads_y = 1;
         d.rows_per_thread = 1;
-        d.prefetch = 6;
     } else {
-        static const int t3[5] = {0, 2, 1, 1, 1};
-        d.t = t3[h->r];
-        d.rows_per_thread = d.t == 1 ? 4 : 2;
+        d.t = 1;
+        d.rows_per_thread = h->r == 1 ? 4 : 2;
         d.threads_x = 16;
         d.threads_y = 8;
-        d.prefetch = 2;
     }
     d.seg = 0;
+    d.prefetch = 0;
     *s = d;
 }
 
@@ -193,91 +191,49 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
               const stencil_schedule &s, const DevInfo &dev, Pass &ps)
 {
     const int D = h->dim, R = h->r;
-    const int es = elem_bytes(dtype);
     const int vy = D == 3 ? s.rows_per_thread : 1;
-    const void *fn = registry().find(D, R, t, vy, dtype);
-    if (!fn) return STENCIL_ERR_UNSUPPORTED;
-    const int TX = s.threads_x, TY = D == 3 ? s.threads_y : 1;
-    if (TX < 8 || TX > 256 || TX % 8 || TY < 1 || TX * TY > stn::kMaxThreads)
-        return STENCIL_ERR_INVALID_ARG;
-    const int Bx = 4 * TX, By = TY * vy;
-    const int htx = round_up((t - 1) * R, 8), hty = (t - 1) * R;
-    const int cx = Bx - 2 * htx, cy = D == 3 ? By - 2 * hty : 1;
-    if (cx < 8 || cy < 1) return STENCIL_ERR_UNSUPPORTED;
-    const int padin = es == 4 ? 4 : 8;
-    const int pw = Bx + 8, ph = D == 3 ? By + 2 * R : 1, pw_in = Bx + 2 * padin;
-    if (D == 3 && (pw_in > 256 || ph > 256)) return STENCIL_ERR_UNSUPPORTED;   // TMA box limits
-    const int plane32 = round_up(pw * ph, 32);
-    const int plane_in = round_up(pw_in * ph * es, 128) / es;
-    const int keep = es == 4 ? R + 2 : 1;   // input slots held besides the prefetched ones
-    const int nring = es == 4 ? t - 1 : t;
-    auto smem_of = [&](int pf) {
-        return static_cast<size_t>(stn::kSmemHeader) +
-               static_cast<size_t>(pf + keep) * plane_in * es +
-               static_cast<size_t>(nring) * (R + 2) * plane32 * 4;
-    };
-    int pf = s.prefetch;
-    if (pf < 1 || pf + keep > stn::kMaxDepthIn) return STENCIL_ERR_INVALID_ARG;
-    while (pf > 1 && smem_of(pf) > static_cast<size_t>(dev.max_smem)) --pf;
-    if (smem_of(pf) > static_cast<size_t>(dev.max_smem)) return STENCIL_ERR_UNSUPPORTED;
-    const size_t smem = smem_of(pf);
-
-    int rc = prepare_fn(fn, dev.max_smem);
+    const stn::KernelEntry *e = registry().find(D, R, t, vy, dtype);
+    if (!e) return STENCIL_ERR_UNSUPPORTED;
+    if ((s.threads_x && s.threads_x != e->tx) || (D == 3 && s.threads_y && s.threads_y != e->ty) ||
+        (s.prefetch && s.prefetch != e->pf))
+        return STENCIL_ERR_UNSUPPORTED;
+    if (e->smem > static_cast<size_t>(dev.max_smem)) return STENCIL_ERR_UNSUPPORTED;
+    int rc = prepare_fn(e->fn, dev.max_smem);
     if (rc) return rc;
     int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, TX * TY, smem));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e->fn, e->tx * e->ty, e->smem));
     if (occ < 1) return STENCIL_ERR_UNSUPPORTED;
 
-    const int64_t ntx = (nx + cx - 1) / cx;
-    const int64_t nty = D == 3 ? (ny + cy - 1) / cy : 1;
+    const int64_t ntx = (nx + e->cx - 1) / e->cx;
+    const int64_t nty = D == 3 ? (ny + e->cy - 1) / e->cy : 1;
     const int64_t ns = D == 3 ? nz : ny;
     const int64_t tiles = ntx * nty;
     int64_t seg = s.seg;
     if (seg <= 0) {
-        // pick the segment length that minimises waves x per-block steps
+        // enough blocks for >= 4 waves (dynamic balance of edge tiles), but segments long
+        // against the pipeline fill of t*(2r+1) planes
         const int64_t slots = static_cast<int64_t>(dev.sms) * occ;
-        double best = 1e300;
-        seg = ns;
-        for (int64_t nseg = 1; nseg <= ns; ++nseg) {
-            const int64_t sg = (ns + nseg - 1) / nseg;
-            const int64_t ne = (ns + sg - 1) / sg;
-            if (ne != nseg) continue;
-            const int64_t blocks = tiles * ne;
-            const int64_t waves = (blocks + slots - 1) / slots;
-            const double cost = static_cast<double>(waves) * (sg + t * R + 8);
-            if (cost < best * 0.999) {
-                best = cost;
-                seg = sg;
-            }
-        }
+        const int64_t want = (4 * slots + tiles - 1) / tiles;
+        const int64_t minseg = std::max<int64_t>(64, 8 * t * (2 * R + 1));
+        seg = std::max<int64_t>((ns + want - 1) / want, minseg);
+        seg = std::min<int64_t>(seg, ns);
     }
     const int64_t nseg = (ns + seg - 1) / seg;
     if (tiles * nseg > 0x7fffffffLL) return STENCIL_ERR_UNSUPPORTED;
 
-    ps.fn = fn;
+    ps.fn = e->fn;
     ps.t = t;
     ps.grid = dim3(static_cast<unsigned>(tiles * nseg));
-    ps.block = dim3(TX, TY);
-    ps.smem = smem;
+    ps.block = dim3(e->tx, e->ty);
+    ps.smem = e->smem;
     stn::SweepArgs &a = ps.a;
     a.nx = static_cast<int>(nx);
     a.ny = static_cast<int>(ny);
     a.nz = static_cast<int>(nz);
     a.ns = static_cast<int>(ns);
-    a.cx = cx;
-    a.cy = cy;
-    a.htx = htx;
-    a.hty = hty;
     a.seg = static_cast<int>(seg);
     a.ntx = static_cast<int>(ntx);
     a.nty = static_cast<int>(nty);
-    a.prefetch = pf;
-    a.depth_in = pf + keep;
-    a.pw = pw;
-    a.ph = ph;
-    a.pw_in = pw_in;
-    a.plane_in = plane_in;
-    a.plane32 = plane32;
     a.timeout_ms = h->timeout_ms;
     a.fault_plane = h->fault_plane;
     a.status = dev.status;
@@ -286,7 +242,7 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
 }
 
 int encode_map(CUtensorMap *m, const void *ptr, int64_t nx, int64_t ny, int64_t nz, int dtype,
-               const stn::SweepArgs &a)
+               int box_w, int box_h)
 {
     auto enc = tensor_map_encoder();
     if (!enc) return STENCIL_ERR_CUDA;
@@ -294,7 +250,7 @@ int encode_map(CUtensorMap *m, const void *ptr, int64_t nx, int64_t ny, int64_t 
     cuuint64_t dims[3] = {static_cast<cuuint64_t>(nx), static_cast<cuuint64_t>(ny),
                           static_cast<cuuint64_t>(nz)};
     cuuint64_t strides[2] = {static_cast<cuuint64_t>(nx * es), static_cast<cuuint64_t>(nx * ny * es)};
-    cuuint32_t box[3] = {static_cast<cuuint32_t>(a.pw_in), static_cast<cuuint32_t>(a.ph), 1};
+    cuuint32_t box[3] = {static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h), 1};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt = dtype == STENCIL_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : dtype == STENCIL_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
@@ -390,7 +346,7 @@ int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny,
         if (user->prefetch) s.prefetch = user->prefetch;
         if (s.t < 0 || s.seg < 0 || s.prefetch < 0) return STENCIL_ERR_INVALID_ARG;
         if (h->dim == 3 && user->t && !user->rows_per_thread)
-            s.rows_per_thread = registry().find(3, h->r, s.t, 4, dtype) ? (s.t == 1 ? 4 : 2) : 2;
+            s.rows_per_thread = (s.t == 1 && registry().find(3, h->r, 1, 4, dtype)) ? 4 : 2;
     }
     const bool aligned = (reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16 == 0;
     const bool streamable = stream_applicable(dtype, nx) && aligned;
@@ -432,7 +388,9 @@ int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny,
             CUtensorMap map;
             std::memset(&map, 0, sizeof(map));
             if (h->dim == 3) {
-                rc = encode_map(&map, src, nx, ny, nz, dtype, ps.a);
+                const int pad = dtype == STENCIL_F32 ? 4 : 8;
+                rc = encode_map(&map, src, nx, ny, nz, dtype, 4 * static_cast<int>(ps.block.x) + 2 * pad,
+                                static_cast<int>(ps.block.y) * s.rows_per_thread + 2 * h->r);
                 if (rc) return rc;
             }
             void *args[] = {&map, &ps.a};

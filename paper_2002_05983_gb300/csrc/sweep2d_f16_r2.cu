@@ -1,19 +1,19 @@
 // Streaming-kernel instantiations: radius 2, __half storage;
-// 2D, every temporal degree whose register queue ((2r+1) rows x 4 cells x t levels) fits.
+// 2D, 128 threads x 4 cells per block row, every temporal degree whose register queue ((2r+1) rows x 4 cells x t levels) fits.
 #include "registry.h"
 #include "sweep_kernel.cuh"
 
 namespace stn {
 namespace {
 const KernelEntry kList[] = {
-    STN_E(2, 2, 1, 1, __half, 2),
-    STN_E(2, 2, 2, 1, __half, 2),
-    STN_E(2, 2, 3, 1, __half, 2),
-    STN_E(2, 2, 4, 1, __half, 2),
-    STN_E(2, 2, 5, 1, __half, 2),
-    STN_E(2, 2, 6, 1, __half, 2),
-    STN_E(2, 2, 7, 1, __half, 2),
-    STN_E(2, 2, 8, 1, __half, 2)};
+    STN_E(2, 2, 1, 1, __half, 2, 128, 1),
+    STN_E(2, 2, 2, 1, __half, 2, 128, 1),
+    STN_E(2, 2, 3, 1, __half, 2, 128, 1),
+    STN_E(2, 2, 4, 1, __half, 2, 128, 1),
+    STN_E(2, 2, 5, 1, __half, 2, 128, 1),
+    STN_E(2, 2, 6, 1, __half, 2, 128, 1),
+    STN_E(2, 2, 7, 1, __half, 2, 128, 1),
+    STN_E(2, 2, 8, 1, __half, 2, 128, 1)};
 }  // namespace
 int list_2d_f16_r2(const KernelEntry **e)
 {

@@ -1,17 +1,17 @@
 // Streaming-kernel instantiations: radius 2, float storage;
-// 3D, 2 or 4 y rows per thread, every temporal degree whose register queue fits.
+// 3D, 16 x 8 threads, 2 or 4 y rows per thread, every temporal degree whose register queue fits.
 #include "registry.h"
 #include "sweep_kernel.cuh"
 
 namespace stn {
 namespace {
 const KernelEntry kList[] = {
-    STN_E(3, 2, 1, 2, float, 0),
-    STN_E(3, 2, 2, 2, float, 0),
-    STN_E(3, 2, 3, 2, float, 0),
-    STN_E(3, 2, 4, 2, float, 0),
-    STN_E(3, 2, 1, 4, float, 0),
-    STN_E(3, 2, 2, 4, float, 0)};
+    STN_E(3, 2, 1, 2, float, 0, 16, 8),
+    STN_E(3, 2, 2, 2, float, 0, 16, 8),
+    STN_E(3, 2, 3, 2, float, 0, 16, 8),
+    STN_E(3, 2, 4, 2, float, 0, 16, 8),
+    STN_E(3, 2, 1, 4, float, 0, 16, 8),
+    STN_E(3, 2, 2, 4, float, 0, 16, 8)};
 }  // namespace
 int list_3d_f32_r2(const KernelEntry **e)
 {

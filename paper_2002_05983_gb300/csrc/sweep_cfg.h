@@ -1,0 +1,48 @@
+// Compile-time geometry of one streaming-kernel instantiation, shared by the
+// kernel and the host planner so both agree on tiles, halos and shared memory.
+#pragma once
+#include <cstddef>
+
+namespace stn {
+
+constexpr int kMaxK = 25;            // 2*3*4 + 1 coefficients
+constexpr int kSmemHeader = 1024;    // mbarriers + abort flag
+constexpr int kMaxDepthIn = 64;
+constexpr unsigned kStatusTimeout = 1u;
+
+__host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ constexpr int rup(int a, int b) { return cdiv(a, b) * b; }
+
+// D: 2 or 3; R: radius; T: time levels per pass; VY: y rows per thread (3D);
+// ES: bytes per stored element (4 fp32, 2 bf16/fp16); TX x TY threads.
+template <int D, int R, int T, int VY, int ES, int TX, int TY> struct Geo {
+    static constexpr int QP = 2 * R + 1;               // register-queue period
+    static constexpr bool F32S = ES == 4;
+    static constexpr int PADIN = 16 / ES;              // input row padding (elements)
+    static constexpr int BX = 4 * TX;                  // thread-region width (cells)
+    static constexpr int BY = (D == 3) ? TY * VY : 1;  // thread-region rows (3D)
+    static constexpr int HTX = rup((T - 1) * R, 8);    // x halo of levels 1..T (multiple of 8)
+    static constexpr int HTY = (D == 3) ? (T - 1) * R : 0;
+    static constexpr int CX = BX - 2 * HTX;            // compute tile (Eq. 2: bsize - 2 t r)
+    static constexpr int CY = (D == 3) ? BY - 2 * HTY : 1;
+    static constexpr int PW = BX + 8;                  // FP32 plane row: 4 pad cells either side
+    static constexpr int PH = (D == 3) ? BY + 2 * R : 1;
+    static constexpr int PWIN = BX + 2 * PADIN;        // input plane row (elements)
+    static constexpr int SLOT32 = rup(PW * PH, 32);    // floats per FP32 ring slot
+    static constexpr int SLOTIN = rup(PWIN * PH * ES, 128) / ES;   // elements per input slot
+    static constexpr int PFMIN = (D == 2) ? 4 : 2;
+    static constexpr int LAG1 = F32S ? R : R + 1;      // steps level 1 trails the input
+    static constexpr int KEEP = F32S ? R + 1 : 1;      // input slots held besides prefetch
+    static constexpr int DEPTH = QP * cdiv(KEEP + PFMIN, QP);   // input ring slots
+    static constexpr int PF = DEPTH - KEEP;            // planes loaded ahead of use
+    static constexpr int NRING = F32S ? T - 1 : T;     // FP32 rings written by the levels
+    static constexpr size_t SMEM = static_cast<size_t>(kSmemHeader) +
+                                   static_cast<size_t>(DEPTH) * SLOTIN * ES +
+                                   static_cast<size_t>(NRING) * QP * SLOT32 * 4;
+    static constexpr bool OK = CX >= 8 && CY >= 1 && DEPTH <= kMaxDepthIn &&
+                               (D == 2 || (PWIN <= 256 && PH <= 256));
+    // step at which level s handles plane p: p + lag(s)
+    __host__ __device__ static constexpr int lag(int s) { return s == 0 ? 0 : LAG1 + (s - 1) * (R + 1); }
+};
+
+}  // namespace stn

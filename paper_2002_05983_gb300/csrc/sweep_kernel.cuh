@@ -39,30 +39,20 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "sweep_cfg.h"
+
 namespace stn {
 
-constexpr int kMaxK = 25;            // 2*3*4 + 1 coefficients
 constexpr int kMaxThreads = 256;
-constexpr int kMaxDepthIn = 64;      // input ring slots (one mbarrier each)
-constexpr int kSmemHeader = 1024;    // mbarriers + abort flag
-constexpr unsigned kStatusTimeout = 1u;
 
 struct SweepArgs {
-    const void *in;       // source grid (2D path reads it with bulk copies)
+    const void *in;       // source grid (the 2D path reads rows with bulk copies)
     void *out;            // destination grid
     unsigned *status;     // sticky device status word
     int nx, ny, nz;       // grid extents (2D: nz = 1)
     int ns;               // extent of the streaming axis (2D: ny, 3D: nz)
-    int cx, cy;           // compute tile extents (x, and y in 3D)
-    int htx, hty;         // thread-region halo around the compute tile
     int seg;              // streaming-axis extent per block
     int ntx, nty;         // tile counts in x and y (nty = 1 in 2D)
-    int depth_in;         // input ring slots
-    int prefetch;         // planes loaded ahead of use
-    int pw, ph;           // padded FP32 plane: (4*TX + 8) x (rows + 2r) (2D: ph = 1)
-    int pw_in;            // padded input plane width in storage elements
-    int plane_in;         // input ring slot stride (storage elements, 128-byte multiple)
-    int plane32;          // FP32 ring slot stride (floats, 128-byte multiple)
     int timeout_ms;       // limit of every bounded wait
     int fault_plane;      // test hook: never load this input plane (< 0: off)
     float c[kMaxK];       // coefficients, Eq. 1 order
@@ -87,6 +77,11 @@ __device__ __forceinline__ void fence_mbar_init()
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
@@ -291,29 +286,36 @@ __device__ __forceinline__ void ghost_fill(float *plane, const Ghost &g, int pw,
 }
 
 // ------------------------------------------------------------------ kernel
-template <int D, int R, int T, int VY, typename S>
-__global__ void __launch_bounds__(kMaxThreads)
+template <int D, int R, int T, int VY, typename S, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY)
     sweep_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ SweepArgs a)
 {
+    using G = Geo<D, R, T, VY, static_cast<int>(sizeof(S)), TX, TY>;
     static_assert(D == 2 || D == 3, "dim");
     static_assert(R >= 1 && R <= 4, "radius");
-    static_assert(D == 3 || VY == 1, "2D keeps one row per thread");
-    constexpr int QP = 2 * R + 1;                 // register queue period
-    constexpr int RD = R + 2;                     // FP32 ring depth
-    constexpr bool F32S = std::is_same<S, float>::value;
-    constexpr int PADIN = Fmt<S>::pad;
-    constexpr int K2 = 2 * D;                     // coefficients per distance
+    static_assert(D == 3 || (VY == 1 && TY == 1), "2D keeps one row per thread");
+    static_assert(G::OK, "tile too small for this temporal degree");
+    constexpr int QP = G::QP;
+    constexpr bool F32S = G::F32S;
+    constexpr int PADIN = G::PADIN;
+    constexpr int K2 = 2 * D;
+    constexpr int PW = G::PW, PWIN = G::PWIN;
+    constexpr int NTHR = TX * TY;
+    constexpr int DEPTH = G::DEPTH;
+    constexpr int SLOT32 = G::SLOT32, SLOTIN = G::SLOTIN;
 
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     volatile int *sflag = reinterpret_cast<volatile int *>(smem + 8 * kMaxDepthIn);
     S *ring_in = reinterpret_cast<S *>(smem + kSmemHeader);
-    float *rings = reinterpret_cast<float *>(smem + kSmemHeader +
-                                             static_cast<size_t>(a.depth_in) * a.plane_in * sizeof(S));
+    float *rings = reinterpret_cast<float *>(smem + kSmemHeader + DEPTH * SLOTIN * sizeof(S));
+    // FP32 ring of level s (F32S: levels 1..T-1, else 0..T-1), slot j = plane mod QP
+    auto ring32 = [&](int s, int j) -> float * {
+        return rings + ((F32S ? s - 1 : s) * QP + j) * SLOT32;
+    };
 
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int nthr = blockDim.x * blockDim.y;
-    const int tid = ty * blockDim.x + tx;
+    const int tid = ty * TX + tx;
 
     // ---- tile and segment of this block
     int b = blockIdx.x;
@@ -324,35 +326,38 @@ __global__ void __launch_bounds__(kMaxThreads)
         tile_y = b % a.nty;
         b /= a.nty;
     }
-    const int gx0 = tile_x * a.cx - a.htx;           // thread-region origin
-    const int gy0 = (D == 3) ? tile_y * a.cy - a.hty : 0;
-    const int ox = gx0 - 4;                          // padded FP32 plane origin
+    const int gx0 = tile_x * G::CX - G::HTX;          // thread-region origin
+    const int gy0 = (D == 3) ? tile_y * G::CY - G::HTY : 0;
+    const int ox = gx0 - 4;                            // padded FP32 plane origin
     const int oy = (D == 3) ? gy0 - R : 0;
-    const int ox_in = gx0 - PADIN;                   // padded input plane origin
+    const int ox_in = gx0 - PADIN;                     // padded input plane origin
     const int Z0 = b * a.seg;
     const int Z1 = min(Z0 + a.seg, a.ns);
     const int last = a.ns - 1;
 
     // ---- this thread's cells
     const int xl = 4 * tx;
-    const int px = xl + 4;                           // padded FP32 column of own cell 0
-    const int px_in = xl + PADIN;
     const int yl0 = ty * VY;
-    const int prow0 = (D == 3) ? yl0 + R : 0;        // padded row of own row 0
+    const int prow0 = (D == 3) ? yl0 + R : 0;          // padded row of own row 0
+    const int toff = prow0 * PW + xl + 4;              // own cell 0 in an FP32 plane
+    const int toffin = prow0 * PWIN + xl + PADIN;      // own cell 0 in an input plane
     const int gx = gx0 + xl;
-    const bool xstore = xl >= a.htx && xl < a.htx + a.cx && gx < a.nx;
+    const bool xstore = xl >= G::HTX && xl < G::HTX + G::CX && gx < a.nx;
     bool ystore[VY];
 #pragma unroll
     for (int vy = 0; vy < VY; ++vy) {
         const int yl = yl0 + vy;
-        ystore[vy] = (D == 2) || (yl >= a.hty && yl < a.hty + a.cy && gy0 + yl < a.ny);
+        ystore[vy] = (D == 2) || (yl >= G::HTY && yl < G::HTY + G::CY && gy0 + yl < a.ny);
     }
+    const int64_t pstride = (D == 3) ? static_cast<int64_t>(a.nx) * a.ny : a.nx;
+    S *const gout = static_cast<S *>(a.out) +
+                    ((D == 3) ? static_cast<int64_t>(gy0 + yl0) * a.nx : 0) + gx;
 
     // A thread whose VY rows cross the grid's top or bottom edge keeps its
     // out-of-grid rows equal to the border row in registers (clamp), since
     // its in-grid rows take y neighbours from its own registers.
-    const int vz = -(gy0 + yl0);                     // own row index of global y = 0
-    const int vb = a.ny - 1 - (gy0 + yl0);           // own row index of global y = ny-1
+    const int vz = -(gy0 + yl0);                       // own row index of global y = 0
+    const int vb = a.ny - 1 - (gy0 + yl0);             // own row index of global y = ny-1
     const bool top_cross = (D == 3) && VY > 1 && vz > 0 && vz < VY;
     const bool bot_cross = (D == 3) && VY > 1 && vb >= 0 && vb < VY - 1;
     auto clamp_rows = [&](float (&v)[VY][4]) {
@@ -372,54 +377,55 @@ __global__ void __launch_bounds__(kMaxThreads)
         }
     };
 
-    // ---- plane ranges per level: level s covers planes [lo[s], hi[s]] at steps p + s*(R+1)
+    // ---- plane ranges: level s covers planes [lo[s], hi[s]], plane p at step p + lag(s)
     int lo[T + 1], hi[T + 1];
+    int kA = 0, kB = 0x7fffffff;
 #pragma unroll
     for (int s = 0; s <= T; ++s) {
         lo[s] = max(Z0 - (T - s) * R, 0);
         hi[s] = Z1 - 1 + (T - s) * R;
+        kA = max(kA, max(lo[s], 1) + G::lag(s));
+        kB = min(kB, min(hi[s], last) + G::lag(s));
     }
+    // steps in [kA, kB] have every level active, inside the grid and past plane 0
     const int k0 = lo[0];
-    const int k1 = Z1 - 1 + T * (R + 1);
-    const int lmax = min(hi[0], last);               // last input plane to load
+    const int k1 = Z1 - 1 + G::lag(T);
+    const int lmax = min(hi[0], last);                 // last input plane to load
+    const int lap0 = k0 / DEPTH;
 
-    const Ghost gh = make_ghost(ox, oy, a.pw, a.ph, a.nx, (D == 3) ? a.ny : 1, R);
-
-    auto ring32 = [&](int s, int slot) -> float * {  // FP32 ring of level s
-        const int idx = F32S ? s - 1 : s;
-        return rings + static_cast<size_t>(idx * RD + slot) * a.plane32;
-    };
+    const Ghost gh = make_ghost(ox, oy, PW, G::PH, a.nx, (D == 3) ? a.ny : 1, R);
 
     if (tid == 0) {
-        for (int i = 0; i < a.depth_in; ++i) mbar_init(smem_addr(bars + i), 1);
+        for (int i = 0; i < DEPTH; ++i) mbar_init(smem_addr(bars + i), 1);
+        // slots before k0's slot are first used one lap later: retire their phase 0 now
+        for (int i = 0; i < k0 % DEPTH; ++i) mbar_arrive(smem_addr(bars + i));
         *sflag = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
-    // thread 0 issues the input loads
+    // thread 0 issues the input loads; plane q goes to slot q mod DEPTH
     int issued_hi = k0 - 1;
     auto issue = [&](int q) {
-        const int slot = (q - k0) % a.depth_in;
+        const int slot = q % DEPTH;
         const uint32_t bar = smem_addr(bars + slot);
-        S *dst = ring_in + static_cast<size_t>(slot) * a.plane_in;
+        S *dst = ring_in + slot * SLOTIN;
         issued_hi = q;
         if (q == a.fault_plane) return;
-        if (D == 2) {
-            const int xa = max(ox_in, 0), xb = min(ox_in + a.pw_in, a.nx);
+        if constexpr (D == 2) {
+            const int xa = max(ox_in, 0), xb = min(ox_in + PWIN, a.nx);
             const uint32_t bytes = xb > xa ? static_cast<uint32_t>((xb - xa) * sizeof(S)) : 0u;
             mbar_arrive_expect_tx(bar, bytes);
             if (bytes)
                 bulk_load(smem_addr(dst + (xa - ox_in)),
-                          static_cast<const S *>(a.in) + static_cast<size_t>(q) * a.nx + xa, bytes,
-                          bar);
+                          static_cast<const S *>(a.in) + static_cast<int64_t>(q) * a.nx + xa, bytes, bar);
         } else {
-            mbar_arrive_expect_tx(bar, static_cast<uint32_t>(a.pw_in * a.ph * sizeof(S)));
+            mbar_arrive_expect_tx(bar, static_cast<uint32_t>(PWIN * G::PH * sizeof(S)));
             tma_load_3d(smem_addr(dst), &tmap, ox_in, oy, q, bar);
         }
     };
     if (tid == 0) {
-        const int qe = min(k0 + a.prefetch - 1, lmax);
+        const int qe = min(k0 + G::PF - 1, lmax);
         for (int q = k0; q <= qe; ++q) issue(q);
     }
 
@@ -433,209 +439,234 @@ __global__ void __launch_bounds__(kMaxThreads)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) q[s][j][vy][v] = 0.f;
 
-    int slot_k = 0;               // input ring slot of plane k
-    int consumed_hi = k0 - 1;     // last input plane waited for by thread 0
+    int consumed_hi = k0 - 1;   // last input plane waited for by thread 0
     bool aborted = false;
-    const int kstart = k0 - k0 % QP;
 
-    for (int kb = kstart; kb <= k1 && !aborted; kb += QP) {
-        SFor<0, QP>::run([&](auto Jc) {
-            constexpr int J = decltype(Jc)::value;
-            const int k = kb + J;
-            if (aborted || k < k0 || k > k1) return;
+    // per-chunk state (a chunk is QP steps; kb is a multiple of QP)
+    int kb = k0 - k0 % QP;
+    int kb_mod = kb % DEPTH;
+    int lap = kb / DEPTH;
+    uint32_t bar0 = 0, par = 0;
+    const S *inb = nullptr;     // own cell 0 in the input slot of plane kb
+    const S *inbp = nullptr;    // own cell 0 in the input slot of plane kb - QP
+    S *inslot = nullptr;        // input slot of plane kb
 
-            // (a) keep `prefetch` input planes in flight
-            if (tid == 0) {
-                const int qn = k + a.prefetch;
-                if (qn <= lmax) {
-                    fence_proxy_async_smem();
-                    issue(qn);
+    // ---- one time level s of step k
+    auto level = [&](auto sc, auto Jc, auto CKc, int k) {
+        constexpr int s = decltype(sc)::value;
+        constexpr int J = decltype(Jc)::value;
+        constexpr bool CK = decltype(CKc)::value;
+        constexpr int js = cmod(J - G::lag(s), QP);    // queue/ring slot of plane p
+        const int p = k - G::lag(s);
+        if constexpr (CK) {
+            if (p < lo[s] || p > hi[s]) return;
+            if (p > last) {   // beyond the end of the stream: repeat the last plane (clamp)
+                if constexpr (s < T) {
+#pragma unroll
+                    for (int vy = 0; vy < VY; ++vy)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) q[s][js][vy][v] = q[s][cmod(js - 1, QP)][vy][v];
                 }
+                return;
             }
-
-            // (b) time levels T..1
-            SFor<0, T>::run([&](auto sc) {
-                constexpr int s = T - decltype(sc)::value;
-                constexpr int js = cmod(J - s * (R + 1), QP);   // queue slot of plane p
-                const int p = k - s * (R + 1);
-                if (p < lo[s] || p > hi[s]) return;
-                if (p > last) {
-                    if constexpr (s < T) {
+        }
+        // level s-1's plane p in shared memory, at this thread's cell 0
+        const float *own;
+        if constexpr (F32S && s == 1) {
+            constexpr int d = J - R;    // input slot of plane k-R relative to plane kb
+            own = reinterpret_cast<const float *>(d >= 0 ? inb + d * SLOTIN : inbp + (d + QP) * SLOTIN);
+        } else {
+            own = ring32(s - 1, js) + toff;
+        }
+        float up[(D == 3) ? R : 1][4], dn[(D == 3) ? R : 1][4];
+        (void)up;
+        (void)dn;
+        if constexpr (D == 3) {
+#pragma unroll
+            for (int m = 0; m < R; ++m) {
+                Fmt<float>::load4(own - (m + 1) * PW, up[m]);
+                Fmt<float>::load4(own + (VY + m) * PW, dn[m]);
+            }
+        }
+        float res[VY][4];
+#pragma unroll
+        for (int vy = 0; vy < VY; ++vy) {
+            float L[4], Rr[4];
+            Fmt<float>::load4(own + vy * PW - 4, L);
+            Fmt<float>::load4(own + vy * PW + 4, Rr);
+            const float(&ctr)[VY][4] = q[s - 1][js];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                float acc = __fmul_rn(a.c[0], ctr[vy][v]);
+#pragma unroll
+                for (int i = 1; i <= R; ++i) {
+                    const int cb = 1 + (i - 1) * K2;
+                    const float w = (v - i >= 0) ? ctr[vy][cclamp(v - i, 0, 3)] : L[cclamp(4 + v - i, 0, 3)];
+                    const float e = (v + i <= 3) ? ctr[vy][cclamp(v + i, 0, 3)] : Rr[cclamp(v + i - 4, 0, 3)];
+                    acc = __fmaf_rn(a.c[cb + 0], w, acc);
+                    acc = __fmaf_rn(a.c[cb + 1], e, acc);
+                    if constexpr (D == 3) {
+                        const float sv = (vy - i >= 0) ? ctr[cclamp(vy - i, 0, VY - 1)][v]
+                                                       : up[cclamp(i - vy - 1, 0, R - 1)][v];
+                        const float nv = (vy + i < VY) ? ctr[cclamp(vy + i, 0, VY - 1)][v]
+                                                       : dn[cclamp(vy + i - VY, 0, R - 1)][v];
+                        acc = __fmaf_rn(a.c[cb + 2], sv, acc);
+                        acc = __fmaf_rn(a.c[cb + 3], nv, acc);
+                    }
+                    acc = __fmaf_rn(a.c[cb + K2 - 2], q[s - 1][cmod(js - i, QP)][vy][v], acc);
+                    acc = __fmaf_rn(a.c[cb + K2 - 1], q[s - 1][cmod(js + i, QP)][vy][v], acc);
+                }
+                res[vy][v] = acc;
+            }
+        }
+        if constexpr (D == 3 && VY > 1) clamp_rows(res);
+        if constexpr (s == T) {
+            if (xstore) {
+                S *o = gout + static_cast<int64_t>(p) * pstride;
+#pragma unroll
+                for (int vy = 0; vy < VY; ++vy)
+                    if (ystore[vy]) Fmt<S>::store4(o + vy * a.nx, res[vy]);
+            }
+        } else {
+            float *dst = ring32(s, js) + toff;
+#pragma unroll
+            for (int vy = 0; vy < VY; ++vy) {
+                Fmt<float>::store4(dst + vy * PW, res[vy]);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) q[s][js][vy][v] = res[vy][v];
+            }
+            if constexpr (CK) {
+                if (p == 0) {   // top clamp: planes -r..-1 of this level equal plane 0
+#pragma unroll
+                    for (int j = 0; j < QP; ++j)
 #pragma unroll
                         for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
-                            for (int v = 0; v < 4; ++v)
-                                q[s][js][vy][v] = q[s][cmod(js - 1, QP)][vy][v];
-                    }
-                    return;
-                }
-                // level s-1's plane p in shared memory
-                const float *src;
-                if (F32S && s == 1) {
-                    int sl = slot_k - (R + 1);
-                    if (sl < 0) sl += a.depth_in;
-                    src = reinterpret_cast<const float *>(ring_in) + static_cast<size_t>(sl) * a.plane_in;
-                } else {
-                    src = ring32(s - 1, p % RD);
-                }
-                const float *own = src + prow0 * a.pw + px;
-                float up[(D == 3) ? R : 1][4], dn[(D == 3) ? R : 1][4];
-                (void)up;
-                (void)dn;
-                if constexpr (D == 3) {
-#pragma unroll
-                    for (int m = 0; m < R; ++m) {
-                        Fmt<float>::load4(own - (m + 1) * a.pw, up[m]);
-                        Fmt<float>::load4(own + (VY + m) * a.pw, dn[m]);
-                    }
-                }
-                float res[VY][4];
-#pragma unroll
-                for (int vy = 0; vy < VY; ++vy) {
-                    float L[4], Rr[4];
-                    Fmt<float>::load4(own + vy * a.pw - 4, L);
-                    Fmt<float>::load4(own + vy * a.pw + 4, Rr);
-                    const float(&ctr)[VY][4] = q[s - 1][js];
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        float acc = __fmul_rn(a.c[0], ctr[vy][v]);
-#pragma unroll
-                        for (int i = 1; i <= R; ++i) {
-                            const int cb = 1 + (i - 1) * K2;
-                            const float w = (v - i >= 0) ? ctr[vy][cclamp(v - i, 0, 3)]
-                                                         : L[cclamp(4 + v - i, 0, 3)];
-                            const float e = (v + i <= 3) ? ctr[vy][cclamp(v + i, 0, 3)]
-                                                         : Rr[cclamp(v + i - 4, 0, 3)];
-                            acc = __fmaf_rn(a.c[cb + 0], w, acc);
-                            acc = __fmaf_rn(a.c[cb + 1], e, acc);
-                            if constexpr (D == 3) {
-                                const float sv = (vy - i >= 0) ? ctr[cclamp(vy - i, 0, VY - 1)][v]
-                                                               : up[cclamp(i - vy - 1, 0, R - 1)][v];
-                                const float nv = (vy + i < VY) ? ctr[cclamp(vy + i, 0, VY - 1)][v]
-                                                               : dn[cclamp(vy + i - VY, 0, R - 1)][v];
-                                acc = __fmaf_rn(a.c[cb + 2], sv, acc);
-                                acc = __fmaf_rn(a.c[cb + 3], nv, acc);
-                            }
-                            acc = __fmaf_rn(a.c[cb + K2 - 2], q[s - 1][cmod(js - i, QP)][vy][v], acc);
-                            acc = __fmaf_rn(a.c[cb + K2 - 1], q[s - 1][cmod(js + i, QP)][vy][v], acc);
-                        }
-                        res[vy][v] = acc;
-                    }
-                }
-                if constexpr (D == 3 && VY > 1) clamp_rows(res);
-                if constexpr (s == T) {
-                    if (xstore) {
-#pragma unroll
-                        for (int vy = 0; vy < VY; ++vy) {
-                            if (!ystore[vy]) continue;
-                            size_t off;
-                            if (D == 2) off = static_cast<size_t>(p) * a.nx + gx;
-                            else off = (static_cast<size_t>(p) * a.ny + (gy0 + yl0 + vy)) * a.nx + gx;
-                            Fmt<S>::store4(static_cast<S *>(a.out) + off, res[vy]);
-                        }
-                    }
-                } else {
-                    float *dst = ring32(s, p % RD) + prow0 * a.pw + px;
-#pragma unroll
-                    for (int vy = 0; vy < VY; ++vy) {
-                        Fmt<float>::store4(dst + vy * a.pw, res[vy]);
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) q[s][js][vy][v] = res[vy][v];
-                    }
-                    if (p == 0) {   // top clamp: planes -r..-1 of this level equal plane 0
-#pragma unroll
-                        for (int j = 0; j < QP; ++j)
-#pragma unroll
-                            for (int vy = 0; vy < VY; ++vy)
-#pragma unroll
-                                for (int v = 0; v < 4; ++v) q[s][j][vy][v] = res[vy][v];
-                    }
-                }
-            });
-
-            // (c) level 0: take plane k from the input ring
-            {
-                constexpr int j0 = J;
-                const int p = k;
-                if (p >= lo[0] && p <= hi[0]) {
-                    if (p > last) {
-#pragma unroll
-                        for (int vy = 0; vy < VY; ++vy)
-#pragma unroll
-                            for (int v = 0; v < 4; ++v) q[0][j0][vy][v] = q[0][cmod(j0 - 1, QP)][vy][v];
-                    } else {
-                        const uint32_t parity = static_cast<uint32_t>(((p - k0) / a.depth_in) & 1);
-                        const bool ok = mbar_wait_bounded(smem_addr(bars + slot_k), parity, a.timeout_ms);
-                        if (!ok) {
-                            *sflag = 1;
-                            atomicOr(a.status, kStatusTimeout);
-                        } else {
-                            if (tid == 0) consumed_hi = p;
-                            const S *inp = ring_in + static_cast<size_t>(slot_k) * a.plane_in;
-                            if constexpr (!F32S) {
-                                // convert the whole padded plane to the level-0 FP32 ring
-                                float *dst = ring32(0, p % RD);
-                                const int c4 = a.pw / 4;
-                                for (int t = tid; t < c4 * a.ph; t += nthr) {
-                                    const int row = t / c4, col = t % c4;
-                                    float v4[4];
-                                    Fmt<S>::load4(inp + row * a.pw_in + 4 * col + (PADIN - 4), v4);
-                                    Fmt<float>::store4(dst + row * a.pw + 4 * col, v4);
-                                }
-                            }
-                            float v4[VY][4];
-#pragma unroll
-                            for (int vy = 0; vy < VY; ++vy)
-                                Fmt<S>::load4(inp + (prow0 + vy) * a.pw_in + px_in, v4[vy]);
-                            if constexpr (D == 3 && VY > 1) clamp_rows(v4);
-#pragma unroll
-                            for (int vy = 0; vy < VY; ++vy)
-#pragma unroll
-                                for (int v = 0; v < 4; ++v) q[0][j0][vy][v] = v4[vy][v];
-                            if (p == 0) {
-#pragma unroll
-                                for (int j = 0; j < QP; ++j)
-#pragma unroll
-                                    for (int vy = 0; vy < VY; ++vy)
-#pragma unroll
-                                        for (int v = 0; v < 4; ++v) q[0][j][vy][v] = q[0][j0][vy][v];
-                            }
-                        }
-                    }
+                            for (int v = 0; v < 4; ++v) q[s][j][vy][v] = res[vy][v];
                 }
             }
+        }
+    };
 
-            // (d) clamp frame of the planes that levels 0..T-1 produced in the previous step
-            if (gh.ntask > 0) {
+    // ---- level 0 of step k: take plane k from the input ring
+    auto level0 = [&](auto Jc, auto CKc, int k) {
+        constexpr int J = decltype(Jc)::value;
+        constexpr bool CK = decltype(CKc)::value;
+        const int p = k;
+        if constexpr (CK) {
+            if (p < lo[0] || p > hi[0]) return;
+            if (p > last) {
 #pragma unroll
-                for (int s = 0; s < T; ++s) {
-                    const int p = k - 1 - s * (R + 1);
-                    if (p < lo[s] || p > min(hi[s], last)) continue;
-                    float *pl;
-                    if (F32S && s == 0) {
-                        int sl = slot_k - 1;
-                        if (sl < 0) sl += a.depth_in;
-                        pl = reinterpret_cast<float *>(ring_in) + static_cast<size_t>(sl) * a.plane_in;
-                    } else {
-                        pl = ring32(s, p % RD);
-                    }
-                    ghost_fill(pl, gh, a.pw, ox, a.nx, tid, nthr);
-                }
+                for (int vy = 0; vy < VY; ++vy)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) q[0][J][vy][v] = q[0][cmod(J - 1, QP)][vy][v];
+                return;
             }
+        }
+        if (!mbar_wait_bounded(bar0 + 8 * J, par, a.timeout_ms)) {
+            *sflag = 1;
+            atomicOr(a.status, kStatusTimeout);
+            return;
+        }
+        if (tid == 0) consumed_hi = p;
+        const S *slot = inslot + J * SLOTIN;
+        if constexpr (!F32S) {
+            // convert the whole padded plane into level 0's FP32 ring
+            float *dst = ring32(0, J);
+            constexpr int C4 = PW / 4;
+            for (int t = tid; t < C4 * G::PH; t += NTHR) {
+                const int row = t / C4, col = t % C4;
+                float v4[4];
+                Fmt<S>::load4(slot + row * PWIN + 4 * col + (PADIN - 4), v4);
+                Fmt<float>::store4(dst + row * PW + 4 * col, v4);
+            }
+        }
+        float v4[VY][4];
+#pragma unroll
+        for (int vy = 0; vy < VY; ++vy) Fmt<S>::load4(inb + J * SLOTIN + vy * PWIN, v4[vy]);
+        if constexpr (D == 3 && VY > 1) clamp_rows(v4);
+#pragma unroll
+        for (int vy = 0; vy < VY; ++vy)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) q[0][J][vy][v] = v4[vy][v];
+        if constexpr (CK) {
+            if (p == 0) {
+#pragma unroll
+                for (int j = 0; j < QP; ++j)
+#pragma unroll
+                    for (int vy = 0; vy < VY; ++vy)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) q[0][j][vy][v] = v4[vy][v];
+            }
+        }
+        if constexpr (F32S) {
+            // the input slot is level 0's ring: clamp its out-of-grid frame now (read from step k+1 on)
+            if (gh.ntask > 0) ghost_fill(reinterpret_cast<float *>(const_cast<S *>(slot)), gh, PW, ox, a.nx, tid, NTHR);
+        }
+    };
 
-            slot_k = (slot_k + 1 == a.depth_in) ? 0 : slot_k + 1;
-            __syncthreads();
-            aborted = (*sflag != 0);
+    // ---- one step
+    auto step = [&](auto Jc, auto CKc) {
+        constexpr int J = decltype(Jc)::value;
+        constexpr bool CK = decltype(CKc)::value;
+        const int k = kb + J;
+        if (aborted) return;
+        if constexpr (CK) {
+            if (k < k0 || k > k1) return;
+        }
+        // keep PF input planes in flight
+        if (tid == 0) {
+            const int qn = k + G::PF;
+            if (qn <= lmax) {
+                if (gh.ntask > 0) fence_proxy_async_smem();
+                issue(qn);
+            }
+        }
+        // levels T..2 (and 1 when it reads a thread-written ring), highest first
+        constexpr int LOW = F32S ? 2 : 1;
+        SFor<0, T - LOW + 1>::run([&](auto ic) {
+            constexpr int s = T - decltype(ic)::value;
+            level(IC<s>{}, Jc, CKc, k);
         });
+        level0(Jc, CKc, k);
+        if constexpr (F32S) level(IC<1>{}, Jc, CKc, k);
+        // clamp frame of ring planes written in the previous step
+        if (gh.ntask > 0) {
+            SFor<F32S ? 1 : 0, T>::run([&](auto sc) {
+                constexpr int s = decltype(sc)::value;
+                const int p = k - 1 - G::lag(s);
+                if (p >= lo[s] && p <= min(hi[s], last))
+                    ghost_fill(ring32(s, cmod(J - 1 - G::lag(s), QP)), gh, PW, ox, a.nx, tid, NTHR);
+            });
+        }
+        __syncthreads();
+        aborted = (*sflag != 0);
+    };
+
+    for (; kb <= k1 && !aborted; kb += QP) {
+        par = static_cast<uint32_t>((lap - lap0) & 1);
+        bar0 = smem_addr(bars + kb_mod);
+        inslot = ring_in + kb_mod * SLOTIN;
+        inb = inslot + toffin;
+        inbp = ring_in + (kb_mod == 0 ? DEPTH - QP : kb_mod - QP) * SLOTIN + toffin;
+        if (kb >= kA && kb + QP - 1 <= kB) {
+            SFor<0, QP>::run([&](auto Jc) { step(Jc, std::false_type{}); });
+        } else {
+            SFor<0, QP>::run([&](auto Jc) { step(Jc, std::true_type{}); });
+        }
+        kb_mod += QP;
+        if (kb_mod == DEPTH) {
+            kb_mod = 0;
+            ++lap;
+        }
     }
 
     if (aborted && tid == 0) {
         // let the copies still in flight land before the block's shared memory is released
         for (int qq = consumed_hi + 1; qq <= issued_hi; ++qq) {
             if (qq == a.fault_plane) continue;
-            const int slot = (qq - k0) % a.depth_in;
-            const uint32_t parity = static_cast<uint32_t>(((qq - k0) / a.depth_in) & 1);
-            mbar_wait_bounded(smem_addr(bars + slot), parity, a.timeout_ms);
+            mbar_wait_bounded(smem_addr(bars + qq % DEPTH), static_cast<uint32_t>((qq / DEPTH - lap0) & 1),
+                              a.timeout_ms);
         }
     }
 }

@@ -50,7 +50,7 @@ def test_2d_stream_bit_exact(r, t):
     iters = 2 * t + 1
     want = oracle.sweep_f32(f, 2, r, c, iters)
     s = st.Stencil(2, r, c)
-    got = run_gpu(s, torch.from_numpy(f), iters, kernel=st.KERNEL_STREAM, t=t, threads_x=64, seg=97)
+    got = run_gpu(s, torch.from_numpy(f), iters, kernel=st.KERNEL_STREAM, t=t, seg=97)
     assert_bits_equal(got, want, f"2D r={r} t={t}")
     w64 = oracle.sweep_f64(f.astype(np.float64), 2, r, c.astype(np.float64), iters)
     assert np.max(np.abs(got.numpy() - w64)) <= 2e-6 * iters
@@ -68,8 +68,7 @@ def test_3d_stream_bit_exact(r, t, vy):
     iters = 2 * t + 1
     want = oracle.sweep_f32(f, 3, r, c, iters)
     s = st.Stencil(3, r, c)
-    got = run_gpu(s, torch.from_numpy(f), iters, kernel=st.KERNEL_STREAM, t=t, threads_x=16,
-                  threads_y=8 if vy == 2 else 4, rows_per_thread=vy, seg=19)
+    got = run_gpu(s, torch.from_numpy(f), iters, kernel=st.KERNEL_STREAM, t=t, rows_per_thread=vy, seg=19)
     assert_bits_equal(got, want, f"3D r={r} t={t} vy={vy}")
 
 
@@ -83,15 +82,11 @@ def test_schedules_bit_identical_to_naive(dim, r):
     x = torch.from_numpy(f)
     iters = 7
     ref = run_gpu(s, x, iters, kernel=st.KERNEL_NAIVE)
-    tmax = st.stencil_max_t(dim, r, 0, 2)
     scheds = []
-    for t in range(1, tmax + 1):
-        if dim == 2:
-            for tx in (32, 128, 256):
-                scheds.append(dict(kernel=st.KERNEL_STREAM, t=t, threads_x=tx, seg=0, prefetch=1 + t % 4))
-        else:
-            scheds.append(dict(kernel=st.KERNEL_STREAM, t=t, threads_x=8, threads_y=16, rows_per_thread=2))
-            scheds.append(dict(kernel=st.KERNEL_STREAM, t=t, threads_x=24, threads_y=8, rows_per_thread=2, seg=5))
+    for vy in ((1,) if dim == 2 else (2, 4)):
+        for t in range(1, st.stencil_max_t(dim, r, 0, vy) + 1):
+            for seg in (0, 7, 61):
+                scheds.append(dict(kernel=st.KERNEL_STREAM, t=t, seg=seg, rows_per_thread=vy))
     for sc in scheds:
         try:
             got = run_gpu(s, x, iters, **sc)
