@@ -170,14 +170,14 @@ void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz,
     stencil_schedule d{};
     d.kernel = stream_applicable(dtype, nx) ? STENCIL_KERNEL_STREAM : STENCIL_KERNEL_NAIVE;
     if (h->dim == 2) {
-        static const int t2[5] = {0, 6, 4, 2, 2};
+        static const int t2[5] = {0, 5, 3, 2, 2};
         d.t = std::min(t2[h->r], reg.max_t(2, h->r, dtype, 1));
         d.threads_x = 128;
         d.threads_y = 1;
         d.rows_per_thread = 1;
     } else {
-        d.t = 1;
-        d.rows_per_thread = h->r == 1 ? 4 : 2;
+        d.t = h->r == 1 ? 2 : 1;
+        d.rows_per_thread = 2;
         d.threads_x = 16;
         d.threads_y = 8;
     }
@@ -346,7 +346,7 @@ int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny,
         if (user->prefetch) s.prefetch = user->prefetch;
         if (s.t < 0 || s.seg < 0 || s.prefetch < 0) return STENCIL_ERR_INVALID_ARG;
         if (h->dim == 3 && user->t && !user->rows_per_thread)
-            s.rows_per_thread = (s.t == 1 && registry().find(3, h->r, 1, 4, dtype)) ? 4 : 2;
+            s.rows_per_thread = 2;
     }
     const bool aligned = (reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16 == 0;
     const bool streamable = stream_applicable(dtype, nx) && aligned;
