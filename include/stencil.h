@@ -140,6 +140,30 @@ int stencil_get_device_status(void *stream, int clear);
  * plane < 0 restores normal operation (and the default 2000 ms limit). */
 int stencil_set_fault_injection(stencil_handle h, int plane, int timeout_ms);
 
+/* stencil_run without any device memory allocation, for callers that cannot
+ * allocate: code that runs while a CUDA graph is being captured (where
+ * cudaMalloc is not allowed), code inside an allocator's out-of-memory path,
+ * or processes whose device memory is handed out by an external budget.
+ * The paper has no counterpart; this is a library-level variant.
+ *  - The second grid of the ping-pong between passes is a 16 MiB array
+ *    compiled into the library (every GPU that loads the library holds it
+ *    until the process exits), so nx*ny*nz*sizeof(dtype) must be at most
+ *    16 MiB (4M FP32 cells, 8M BF16/FP16 cells); larger grids are rejected
+ *    with STENCIL_ERR_INVALID_ARG before any device work.
+ *  - The first call on a device looks up the array's device address and the
+ *    device attributes; make that first call before any stream capture.
+ *  - All calls on a device share the array, which keeps the last call's
+ *    contents: calls whose work overlaps on the GPU (different streams, or
+ *    different handles at the same time) race and give wrong results.
+ *  - The schedule is the one stencil_run would pick (no tuned schedules are
+ *    consulted); results equal stencil_run's bit for bit.
+ *  - A kernel whose bounded wait expires records it in a device word of this
+ *    entry point that each call resets; it is not reported by
+ *    stencil_get_device_status.
+ * Arguments and other errors as stencil_run. */
+int stencil_run_noalloc(stencil_handle h, const void *in, void *out, int64_t nx, int64_t ny,
+                        int64_t nz, int iters, int dtype, void *stream);
+
 /* cudaError_t of the last failed CUDA call on this host thread (0 if none). */
 int stencil_last_cuda_error(void);
 

@@ -30,7 +30,8 @@ KERNEL_AUTO, KERNEL_STREAM, KERNEL_NAIVE = 0, 1, 2
 # every symbol include/stencil.h declares
 EXPORTS = ("stencil_create", "stencil_destroy", "stencil_run", "stencil_run_ex", "stencil_run_host",
            "stencil_default_schedule", "stencil_max_t", "stencil_get_device_status",
-           "stencil_set_fault_injection", "stencil_last_cuda_error", "stencil_strerror")
+           "stencil_set_fault_injection", "stencil_run_noalloc", "stencil_last_cuda_error",
+           "stencil_strerror")
 
 
 class StencilError(RuntimeError):
@@ -74,6 +75,7 @@ def _lib():
                 lib.stencil_max_t.argtypes = [i32, i32, i32, i32]
                 lib.stencil_get_device_status.argtypes = [vp, i32]
                 lib.stencil_set_fault_injection.argtypes = [vp, i32, i32]
+                lib.stencil_run_noalloc.argtypes = [vp, vp, vp, i64, i64, i64, i32, i32, vp]
                 lib.stencil_last_cuda_error.argtypes = []
                 lib.stencil_strerror.argtypes = [i32]
                 lib.stencil_strerror.restype = ctypes.c_char_p
@@ -145,6 +147,12 @@ def stencil_get_device_status(stream=None, clear: bool = False) -> int:
 
 def stencil_set_fault_injection(h, plane: int, timeout_ms: int = 50) -> int:
     return _check(_lib().stencil_set_fault_injection(h, plane, timeout_ms), "stencil_set_fault_injection")
+
+
+def stencil_run_noalloc(h, in_ptr, out_ptr, nx, ny, nz, iters, dtype, stream) -> int:
+    """stencil_run without device allocation (grids up to 16 MiB); see include/stencil.h."""
+    return _check(_lib().stencil_run_noalloc(h, in_ptr, out_ptr, nx, ny, nz, iters, dtype, stream),
+                  "stencil_run_noalloc")
 
 
 def stencil_last_cuda_error() -> int:

@@ -401,6 +401,49 @@ int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny,
     return 0;
 }
 
+// ------------------------------------------------------------------------
+// Scratch for stencil_run_noalloc.  Callers that must not allocate device
+// memory (code running while a CUDA graph is captured, inside an allocator's
+// out-of-memory path, or under an external memory budget) still need the
+// second grid of the ping-pong between passes; it lives in this file-scope
+// array instead, which every GPU that loads the library holds until exit.
+// In host code the array's name is only a stand-in: its device address is
+// fetched once per device with cudaGetSymbolAddress below.
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;   // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+static __device__ __align__(256) unsigned g_noalloc_status[64];
+
+struct NoAllocDev {
+    bool ready = false;
+    void *scratch = nullptr;
+    unsigned *status = nullptr;
+    int sms = 0, max_smem = 0;
+};
+std::mutex g_noalloc_mu;
+NoAllocDev g_noalloc[64];
+
+// Set-up of the current device (first call on that device): symbol
+// addresses and the attributes the planner needs.  Allocates nothing.
+int noalloc_device(NoAllocDev **out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return STENCIL_ERR_NO_DEVICE;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoAllocDev &d = g_noalloc[dev];
+    if (!d.ready) {
+        CK(cudaGetSymbolAddress(&d.scratch, g_noalloc_scratch));
+        void *st = nullptr;
+        CK(cudaGetSymbolAddress(&st, g_noalloc_status));
+        d.status = static_cast<unsigned *>(st);
+        CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaDeviceGetAttribute(&d.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        d.ready = true;
+    }
+    *out = &d;
+    return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -513,6 +556,71 @@ int stencil_set_fault_injection(stencil_handle h, int plane, int timeout_ms)
     if (timeout_ms < 1 || timeout_ms > 10000) return STENCIL_ERR_INVALID_ARG;
     h->fault_plane = plane;
     h->timeout_ms = timeout_ms;
+    return STENCIL_OK;
+}
+
+int stencil_run_noalloc(stencil_handle h, const void *in, void *out, int64_t nx, int64_t ny,
+                        int64_t nz, int iters, int dtype, void *stream)
+{
+    int rc = check_problem(h, in, out, nx, ny, nz, iters, dtype);
+    if (rc) return rc;
+    const size_t bytes = static_cast<size_t>(nx * ny * nz) * elem_bytes(dtype);
+    if (bytes > kNoAllocScratchBytes) return STENCIL_ERR_INVALID_ARG;
+    NoAllocDev *nd = nullptr;
+    rc = noalloc_device(&nd);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the status word must start at zero for this call; the scratch grid needs
+    // no clearing (every pass writes all of it before the next pass reads it)
+    CK(cudaMemsetAsync(nd->status, 0, sizeof(unsigned), st));
+    if (iters == 0) {
+        CK(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st));
+        return STENCIL_OK;
+    }
+    DevInfo dev;
+    dev.sms = nd->sms;
+    dev.max_smem = nd->max_smem;
+    dev.status = nd->status;
+    stencil_schedule s;
+    default_schedule(h, nx, ny, nz, dtype, &s);
+    const bool aligned = (reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16 == 0;
+    const bool streamable = s.kernel == STENCIL_KERNEL_STREAM && aligned;
+    const int t = streamable ? std::max(1, std::min(s.t, iters)) : 1;
+    const int L = (iters + t - 1) / t;
+    const int t_last = iters - (L - 1) * t;
+    Pass full, tail;
+    if (streamable) {
+        rc = plan_pass(h, nx, ny, nz, dtype, t, s, dev, full);
+        if (rc) return rc;
+        if (t_last != t) {
+            rc = plan_pass(h, nx, ny, nz, dtype, t_last, s, dev, tail);
+            if (rc) return rc;
+        }
+    }
+    const void *src = in;
+    for (int j = 0; j < L; ++j) {
+        void *dst = ((L - 1 - j) % 2 == 0) ? out : nd->scratch;
+        if (!streamable) {
+            rc = launch_naive(h, src, dst, nx, ny, nz, dtype, st, dev);
+            if (rc) return rc;
+        } else {
+            Pass &ps = (j == L - 1 && t_last != t) ? tail : full;
+            ps.a.in = src;
+            ps.a.out = dst;
+            ps.a.status = nd->status;
+            CUtensorMap map;
+            std::memset(&map, 0, sizeof(map));
+            if (h->dim == 3) {
+                const int pad = dtype == STENCIL_F32 ? 4 : 8;
+                rc = encode_map(&map, src, nx, ny, nz, dtype, 4 * static_cast<int>(ps.block.x) + 2 * pad,
+                                static_cast<int>(ps.block.y) * s.rows_per_thread + 2 * h->r);
+                if (rc) return rc;
+            }
+            void *args[] = {&map, &ps.a};
+            CK(cudaLaunchKernel(ps.fn, ps.grid, ps.block, args, ps.smem, st));
+        }
+        src = dst;
+    }
     return STENCIL_OK;
 }
 
