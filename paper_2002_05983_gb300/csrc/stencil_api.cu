@@ -68,10 +68,13 @@ struct Registry {
             all.insert(all.end(), e, e + n);
         }
     }
-    const stn::KernelEntry *find(int dim, int r, int t, int vy, int dtype) const
+    // tx / ty = 0: the default block shape (the first listed for that degree)
+    const stn::KernelEntry *find(int dim, int r, int t, int vy, int dtype, int tx = 0, int ty = 0) const
     {
         for (const auto &e : all)
-            if (e.dim == dim && e.r == r && e.t == t && (dim == 2 || e.vy == vy) && e.dtype == dtype) return &e;
+            if (e.dim == dim && e.r == r && e.t == t && (dim == 2 || e.vy == vy) && e.dtype == dtype &&
+                (!tx || e.tx == tx) && (dim == 2 || !ty || e.ty == ty))
+                return &e;
         return nullptr;
     }
     int max_t(int dim, int r, int dtype, int vy) const
@@ -172,14 +175,14 @@ void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz,
     if (h->dim == 2) {
         static const int t2[5] = {0, 5, 3, 2, 2};
         d.t = std::min(t2[h->r], reg.max_t(2, h->r, dtype, 1));
-        d.threads_x = 128;
-        d.threads_y = 1;
+        d.threads_x = 0;
+        d.threads_y = 0;
         d.rows_per_thread = 1;
     } else {
         d.t = h->r == 1 ? 2 : 1;
         d.rows_per_thread = 2;
-        d.threads_x = 16;
-        d.threads_y = 8;
+        d.threads_x = 0;
+        d.threads_y = 0;
     }
     d.seg = 0;
     d.prefetch = 0;
@@ -192,11 +195,9 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
 {
     const int D = h->dim, R = h->r;
     const int vy = D == 3 ? s.rows_per_thread : 1;
-    const stn::KernelEntry *e = registry().find(D, R, t, vy, dtype);
+    const stn::KernelEntry *e = registry().find(D, R, t, vy, dtype, s.threads_x, D == 3 ? s.threads_y : 0);
     if (!e) return STENCIL_ERR_UNSUPPORTED;
-    if ((s.threads_x && s.threads_x != e->tx) || (D == 3 && s.threads_y && s.threads_y != e->ty) ||
-        (s.prefetch && s.prefetch != e->pf))
-        return STENCIL_ERR_UNSUPPORTED;
+    if (s.prefetch && s.prefetch != e->pf) return STENCIL_ERR_UNSUPPORTED;
     if (e->smem > static_cast<size_t>(dev.max_smem)) return STENCIL_ERR_UNSUPPORTED;
     int rc = prepare_fn(e->fn, dev.max_smem);
     if (rc) return rc;
