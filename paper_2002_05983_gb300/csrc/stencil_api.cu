@@ -175,14 +175,14 @@ void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz,
     if (h->dim == 2) {
         static const int t2[5] = {0, 5, 3, 2, 2};
         d.t = std::min(t2[h->r], reg.max_t(2, h->r, dtype, 1));
-        d.threads_x = 0;
-        d.threads_y = 0;
+        d.threads_x = 128;
+        d.threads_y = 1;
         d.rows_per_thread = 1;
     } else {
         d.t = h->r == 1 ? 2 : 1;
         d.rows_per_thread = 2;
-        d.threads_x = 0;
-        d.threads_y = 0;
+        d.threads_x = 16;
+        d.threads_y = 8;
     }
     d.seg = 0;
     d.prefetch = 0;
