@@ -85,6 +85,26 @@ typedef struct {
     int prefetch;        /* 0, or the compiled number of planes loaded ahead */
 } stencil_schedule;
 
+/* Number of features describing one (problem, schedule) pair for the cost model. */
+#define STENCIL_NFEAT 12
+
+/* One measured or predicted schedule of a problem (stencil_tune output). */
+typedef struct {
+    stencil_schedule sched;          /* fully resolved (no 0 fields) */
+    float features[STENCIL_NFEAT];   /* stencil_schedule_features of it */
+    float ns_per_cell;               /* measured ns per cell update (exhaustive), else -1 */
+    float analytic_ns_per_cell;      /* the analytic model's estimate */
+    float model_ns_per_cell;         /* the cost model's estimate, else -1 */
+} stencil_timing;
+
+typedef struct stencil_model *stencil_model_handle;
+
+typedef enum {
+    STENCIL_TUNE_ANALYTIC = 0,   /* pick the minimum of the analytic bandwidth/compute model */
+    STENCIL_TUNE_EXHAUSTIVE = 1, /* time every candidate on the GPU, pick the fastest */
+    STENCIL_TUNE_MODEL = 2       /* pick the minimum predicted by a trained cost model */
+} stencil_tune_mode;
+
 /* Create a stencil of dimension `dim` (2 or 3) and radius 1..4 with
  * K = 2*dim*radius + 1 FP32 coefficients read from host memory `coeffs`
  * (layout above; copied, the caller keeps ownership).  Allocates no device
@@ -122,6 +142,57 @@ int stencil_run_host(stencil_handle h, const void *in_host, void *out_host, int6
 /* The schedule stencil_run would use for this problem (auto choice). */
 int stencil_default_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
                              stencil_schedule *out);
+
+/* Schedule tuner (the model-guided parameter choice of Sections V.A and VI.A,
+ * re-done for the GPU).  Candidates: every compiled temporal degree, several
+ * stream-segment lengths and, in 3D, 2 or 4 rows per thread.
+ *  - ANALYTIC: time per cell update = max(HBM bytes / bandwidth, FP32
+ *    instructions incl. halo redundancy / issue rate) per pass, divided by the
+ *    cell updates of the pass; no device work.
+ *  - EXHAUSTIVE: allocates an input and output grid of the problem's size
+ *    (cudaMalloc), runs each candidate for >= 16 steps after a warm-up, takes
+ *    the best of two CUDA-event timings, frees the grids; synchronous.
+ *  - MODEL: needs `model` (stencil_model_train); no device work besides the
+ *    model's forward pass.
+ * `chosen` receives the pick; `rows` (capacity `cap`, may be NULL) receives one
+ * stencil_timing per candidate and *nrows their number.  With `store` != 0 the
+ * pick is kept in the handle and used by later stencil_run calls on the same
+ * (nx, ny, nz, dtype).  Errors: INVALID_ARG, UNSUPPORTED (no streaming kernel
+ * for this shape), OOM, CUDA. */
+int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype, int mode,
+                 stencil_model_handle model, int store, stencil_schedule *chosen,
+                 stencil_timing *rows, int cap, int *nrows);
+
+/* Features of (problem, schedule) for the cost model: dim, radius, log2 nx,
+ * log2 ny, log2 nz, bytes per element, t, tile width (cells), tile height
+ * (rows, 1 in 2D), threads per block, log2 segment length, log2 analytic ns
+ * per cell update.  `sched` may be partial (0 = library choice). */
+int stencil_schedule_features(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                              const stencil_schedule *sched, float *features);
+
+/* Cost model: `n_features` -> hidden -> hidden -> 1 multilayer perceptron with
+ * ReLU, trained by full-batch Adam on the mean-squared error of its
+ * (standardised) target, with hand-written CUDA forward, backward and update
+ * kernels on the current device.  Host arrays: X is row-major n x n_features,
+ * y has n entries.  Training standardises features and targets on its first
+ * call unless stencil_model_normalization set them.  Errors: INVALID_ARG,
+ * OOM, CUDA. */
+int stencil_model_create(stencil_model_handle *out, int n_features, int hidden, int seed);
+int stencil_model_destroy(stencil_model_handle m);
+int stencil_model_train(stencil_model_handle m, const float *X, const float *y, int n, int epochs,
+                        float lr, float *final_loss);
+int stencil_model_predict(stencil_model_handle m, const float *X, float *y, int n);
+/* Fixed standardisation (x - fmean) / fstd, (y - ymean) / ystd. */
+int stencil_model_normalization(stencil_model_handle m, const float *fmean, const float *fstd,
+                                float ymean, float ystd);
+/* Copy the flat parameters (W1, b1, W2, b2, w3, b3; row-major, input index
+ * first) to (set = 0) or from (set != 0) host memory; returns the parameter
+ * count instead when `count` does not match it. */
+int stencil_model_params(stencil_model_handle m, float *host, int count, int set);
+/* Loss (mean squared error in standardised units) and its gradient with
+ * respect to the flat parameters, for testing the backward kernels. */
+int stencil_model_grad(stencil_model_handle m, const float *X, const float *y, int n, float *loss,
+                       float *grad);
 
 /* Largest temporal degree compiled in for (dim, radius, dtype) and, in 3D,
  * rows_per_thread; 0 if none.  */

@@ -30,8 +30,13 @@ KERNEL_AUTO, KERNEL_STREAM, KERNEL_NAIVE = 0, 1, 2
 # every symbol include/stencil.h declares
 EXPORTS = ("stencil_create", "stencil_destroy", "stencil_run", "stencil_run_ex", "stencil_run_host",
            "stencil_default_schedule", "stencil_max_t", "stencil_get_device_status",
-           "stencil_set_fault_injection", "stencil_run_noalloc", "stencil_last_cuda_error",
-           "stencil_strerror")
+           "stencil_set_fault_injection", "stencil_run_noalloc", "stencil_tune",
+           "stencil_schedule_features", "stencil_model_create", "stencil_model_destroy",
+           "stencil_model_train", "stencil_model_predict", "stencil_model_normalization",
+           "stencil_model_params", "stencil_model_grad", "stencil_last_cuda_error", "stencil_strerror")
+
+NFEAT = 12
+TUNE_ANALYTIC, TUNE_EXHAUSTIVE, TUNE_MODEL = 0, 1, 2
 
 
 class StencilError(RuntimeError):
@@ -49,6 +54,12 @@ class Schedule(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Timing(ctypes.Structure):
+    """stencil_timing: one candidate schedule with its features and times."""
+    _fields_ = [("sched", Schedule), ("features", ctypes.c_float * 12), ("ns_per_cell", ctypes.c_float),
+                ("analytic_ns_per_cell", ctypes.c_float), ("model_ns_per_cell", ctypes.c_float)]
 
 
 _lock = threading.Lock()
@@ -76,6 +87,17 @@ def _lib():
                 lib.stencil_get_device_status.argtypes = [vp, i32]
                 lib.stencil_set_fault_injection.argtypes = [vp, i32, i32]
                 lib.stencil_run_noalloc.argtypes = [vp, vp, vp, i64, i64, i64, i32, i32, vp]
+                fp = ctypes.POINTER(ctypes.c_float)
+                lib.stencil_tune.argtypes = [vp, i64, i64, i64, i32, i32, vp, i32, sp,
+                                             ctypes.POINTER(Timing), i32, ctypes.POINTER(i32)]
+                lib.stencil_schedule_features.argtypes = [vp, i64, i64, i64, i32, sp, fp]
+                lib.stencil_model_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32]
+                lib.stencil_model_destroy.argtypes = [vp]
+                lib.stencil_model_train.argtypes = [vp, fp, fp, i32, i32, ctypes.c_float, fp]
+                lib.stencil_model_predict.argtypes = [vp, fp, fp, i32]
+                lib.stencil_model_normalization.argtypes = [vp, fp, fp, ctypes.c_float, ctypes.c_float]
+                lib.stencil_model_params.argtypes = [vp, fp, i32, i32]
+                lib.stencil_model_grad.argtypes = [vp, fp, fp, i32, fp, fp]
                 lib.stencil_last_cuda_error.argtypes = []
                 lib.stencil_strerror.argtypes = [i32]
                 lib.stencil_strerror.restype = ctypes.c_char_p
@@ -153,6 +175,88 @@ def stencil_run_noalloc(h, in_ptr, out_ptr, nx, ny, nz, iters, dtype, stream) ->
     """stencil_run without device allocation (grids up to 16 MiB); see include/stencil.h."""
     return _check(_lib().stencil_run_noalloc(h, in_ptr, out_ptr, nx, ny, nz, iters, dtype, stream),
                   "stencil_run_noalloc")
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def stencil_tune(h, nx, ny, nz, dtype, mode, model=None, store=True, cap=256):
+    """Returns (chosen Schedule, list of Timing rows)."""
+    chosen = Schedule()
+    rows = (Timing * cap)()
+    n = ctypes.c_int(0)
+    _check(_lib().stencil_tune(h, nx, ny, nz, dtype, mode, model, 1 if store else 0, ctypes.byref(chosen),
+                               rows, cap, ctypes.byref(n)), "stencil_tune")
+    return chosen, [rows[i] for i in range(min(n.value, cap))]
+
+
+def stencil_schedule_features(h, nx, ny, nz, dtype, sched: Schedule | None = None):
+    import numpy as np
+    f = np.zeros(NFEAT, np.float32)
+    _check(_lib().stencil_schedule_features(h, nx, ny, nz, dtype,
+                                            ctypes.byref(sched) if sched is not None else None, _fptr(f)),
+           "stencil_schedule_features")
+    return f
+
+
+def stencil_model_create(n_features=NFEAT, hidden=64, seed=0) -> int:
+    m = ctypes.c_void_p()
+    _check(_lib().stencil_model_create(ctypes.byref(m), n_features, hidden, seed), "stencil_model_create")
+    return m.value
+
+
+def stencil_model_destroy(m) -> int:
+    return _check(_lib().stencil_model_destroy(m), "stencil_model_destroy")
+
+
+def stencil_model_train(m, X, y, epochs=2000, lr=3e-3) -> float:
+    import numpy as np
+    X = np.ascontiguousarray(X, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(_lib().stencil_model_train(m, _fptr(X), _fptr(y), len(y), epochs, lr, _fptr(loss)),
+           "stencil_model_train")
+    return float(loss[0])
+
+
+def stencil_model_predict(m, X):
+    import numpy as np
+    X = np.ascontiguousarray(X, np.float32)
+    y = np.zeros(X.shape[0], np.float32)
+    _check(_lib().stencil_model_predict(m, _fptr(X), _fptr(y), X.shape[0]), "stencil_model_predict")
+    return y
+
+
+def stencil_model_normalization(m, fmean, fstd, ymean, ystd) -> int:
+    import numpy as np
+    a = np.ascontiguousarray(fmean, np.float32)
+    b = np.ascontiguousarray(fstd, np.float32)
+    return _check(_lib().stencil_model_normalization(m, _fptr(a), _fptr(b), ymean, ystd),
+                  "stencil_model_normalization")
+
+
+def stencil_model_params(m, values=None):
+    """Get (values None) or set the flat parameter vector."""
+    import numpy as np
+    n = _lib().stencil_model_params(m, _fptr(np.zeros(1, np.float32)), -1, 0)
+    if values is None:
+        p = np.zeros(n, np.float32)
+        _check(_lib().stencil_model_params(m, _fptr(p), n, 0), "stencil_model_params")
+        return p
+    p = np.ascontiguousarray(values, np.float32)
+    return _check(_lib().stencil_model_params(m, _fptr(p), p.size, 1), "stencil_model_params")
+
+
+def stencil_model_grad(m, X, y):
+    import numpy as np
+    X = np.ascontiguousarray(X, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    n = _lib().stencil_model_params(m, _fptr(np.zeros(1, np.float32)), -1, 0)
+    g = np.zeros(n, np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(_lib().stencil_model_grad(m, _fptr(X), _fptr(y), len(y), _fptr(loss), _fptr(g)), "stencil_model_grad")
+    return float(loss[0]), g
 
 
 def stencil_last_cuda_error() -> int:

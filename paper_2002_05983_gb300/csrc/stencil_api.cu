@@ -2,6 +2,7 @@
 // multi-pass driver (ceil(iters / t) passes ping-ponging between the
 // caller's output and a handle-owned scratch grid) and kernel launches.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -27,6 +28,12 @@ struct stencil_plan {
     int host_dev = -1;
     int fault_plane = -1;
     int timeout_ms = 2000;
+    struct Tuned {
+        int64_t nx, ny, nz;
+        int dtype;
+        stencil_schedule s;
+    };
+    std::vector<Tuned> tuned;   // schedules stored by stencil_tune
 };
 
 namespace {
@@ -336,6 +343,8 @@ int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny,
     }
     stencil_schedule s;
     default_schedule(h, nx, ny, nz, dtype, &s);
+    for (const auto &tu : h->tuned)
+        if (tu.nx == nx && tu.ny == ny && tu.nz == nz && tu.dtype == dtype) s = tu.s;
     if (user) {
         if (user->kernel < 0 || user->kernel > STENCIL_KERNEL_NAIVE) return STENCIL_ERR_INVALID_ARG;
         if (user->kernel) s.kernel = user->kernel;
@@ -400,6 +409,94 @@ int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny,
         src = dst;
     }
     return 0;
+}
+
+// ------------------------------------------------------------------------
+// Schedule tuner: candidates, analytic model, features.
+constexpr double kFp32InstrRate = 152.0 * 128.0 * 2.07e9;   // FP32 lane instructions / s (nominal)
+constexpr double kFpEfficiency = 0.45;                      // fraction reached by the sweep kernels
+constexpr double kHbmBytesPerS = 6792.1e9 * 0.92;           // measured copy bandwidth, achievable share
+
+// Resolve every field of a schedule for a problem (the pass of degree t).
+int resolve(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, stencil_schedule s,
+            const DevInfo &dev, stencil_schedule &out, Pass &ps)
+{
+    int rc = plan_pass(h, nx, ny, nz, dtype, s.t, s, dev, ps);
+    if (rc) return rc;
+    out = s;
+    out.kernel = STENCIL_KERNEL_STREAM;
+    out.threads_x = static_cast<int>(ps.block.x);
+    out.threads_y = static_cast<int>(ps.block.y);
+    out.seg = ps.a.seg;
+    const stn::KernelEntry *e = registry().find(h->dim, h->r, s.t, h->dim == 3 ? s.rows_per_thread : 1, dtype,
+                                                out.threads_x, out.threads_y);
+    out.prefetch = e ? e->pf : 0;
+    if (h->dim == 2) out.rows_per_thread = 1;
+    return 0;
+}
+
+// Analytic time per cell update (ns) of a resolved schedule.
+double analytic_ns(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, const stencil_schedule &s)
+{
+    const int D = h->dim, R = h->r, t = s.t;
+    const stn::KernelEntry *e = registry().find(D, R, t, D == 3 ? s.rows_per_thread : 1, dtype, s.threads_x,
+                                                s.threads_y);
+    if (!e) return 1e9;
+    const double es = elem_bytes(dtype);
+    const double N = static_cast<double>(nx) * ny * nz;
+    const double bx = 4.0 * e->tx, by = D == 3 ? static_cast<double>(e->ty) * e->vy : 1.0;
+    const double tiles = std::ceil(nx / static_cast<double>(e->cx)) * (D == 3 ? std::ceil(ny / static_cast<double>(e->cy)) : 1.0);
+    const double ns_axis = D == 3 ? static_cast<double>(nz) : static_cast<double>(ny);
+    const double nseg = std::ceil(ns_axis / s.seg);
+    // cell-level updates of one pass: every tile computes its thread region for
+    // every level over its segment plus the r*t stream halo
+    const double updates = tiles * nseg * bx * by * t * (s.seg + static_cast<double>(t) * R);
+    const double t_fp = updates * (2.0 * D * R + 1.0) / (kFp32InstrRate * kFpEfficiency);
+    const double t_mem = N * 2.0 * es / kHbmBytesPerS;
+    return std::max(t_fp, t_mem) / (N * t) * 1e9;
+}
+
+void features_of(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, const stencil_schedule &s,
+                 double analytic, float *f)
+{
+    f[0] = static_cast<float>(h->dim);
+    f[1] = static_cast<float>(h->r);
+    f[2] = static_cast<float>(std::log2(static_cast<double>(nx)));
+    f[3] = static_cast<float>(std::log2(static_cast<double>(ny)));
+    f[4] = static_cast<float>(std::log2(static_cast<double>(nz)));
+    f[5] = static_cast<float>(elem_bytes(dtype));
+    f[6] = static_cast<float>(s.t);
+    f[7] = static_cast<float>(4 * s.threads_x);
+    f[8] = static_cast<float>(h->dim == 3 ? s.threads_y * s.rows_per_thread : 1);
+    f[9] = static_cast<float>(s.threads_x * s.threads_y);
+    f[10] = static_cast<float>(std::log2(static_cast<double>(s.seg)));
+    f[11] = static_cast<float>(std::log2(analytic));
+}
+
+// Candidate schedules (unresolved) of a problem.
+int candidates(const stencil_plan *h, int64_t ny, int64_t nz, int dtype, stencil_schedule *out, int cap)
+{
+    int n = 0;
+    const int64_t ns = h->dim == 3 ? nz : ny;
+    const int segs2[] = {0, 128, 256, 512, 1024};
+    const int segs3[] = {0, 32, 64, 128, 256};
+    const int *segs = h->dim == 2 ? segs2 : segs3;
+    for (int vy : {2, 4}) {
+        if (h->dim == 2 && vy == 4) break;
+        const int tmax = registry().max_t(h->dim, h->r, dtype, h->dim == 3 ? vy : 1);
+        for (int t = 1; t <= tmax; ++t)
+            for (int k = 0; k < 5; ++k) {
+                if (segs[k] > ns) continue;
+                if (n >= cap) return n;
+                stencil_schedule s{};
+                s.kernel = STENCIL_KERNEL_STREAM;
+                s.t = t;
+                s.rows_per_thread = h->dim == 3 ? vy : 1;
+                s.seg = segs[k];
+                out[n++] = s;
+            }
+    }
+    return n;
 }
 
 // ------------------------------------------------------------------------
@@ -622,6 +719,131 @@ int stencil_run_noalloc(stencil_handle h, const void *in, void *out, int64_t nx,
         }
         src = dst;
     }
+    return STENCIL_OK;
+}
+
+int stencil_schedule_features(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                              const stencil_schedule *sched, float *features)
+{
+    if (!h || !features || nx <= 0 || ny <= 0 || nz <= 0 || dtype < STENCIL_F32 || dtype > STENCIL_F16)
+        return STENCIL_ERR_INVALID_ARG;
+    DevInfo *dev = nullptr;
+    int rc = device_info(&dev);
+    if (rc) return rc;
+    stencil_schedule s;
+    default_schedule(h, nx, ny, nz, dtype, &s);
+    if (sched) {
+        if (sched->t) s.t = sched->t;
+        if (sched->rows_per_thread) s.rows_per_thread = sched->rows_per_thread;
+        if (sched->seg) s.seg = sched->seg;
+        if (sched->threads_x) s.threads_x = sched->threads_x;
+        if (sched->threads_y) s.threads_y = sched->threads_y;
+    }
+    stencil_schedule r;
+    Pass ps;
+    rc = resolve(h, nx, ny, nz, dtype, s, *dev, r, ps);
+    if (rc) return rc;
+    features_of(h, nx, ny, nz, dtype, r, analytic_ns(h, nx, ny, nz, dtype, r), features);
+    return STENCIL_OK;
+}
+
+int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype, int mode,
+                 stencil_model_handle model, int store, stencil_schedule *chosen, stencil_timing *rows,
+                 int cap, int *nrows)
+{
+    if (!h || !chosen || nx <= 0 || ny <= 0 || nz <= 0 || (h->dim == 2 && nz != 1) || dtype < STENCIL_F32 ||
+        dtype > STENCIL_F16 || mode < STENCIL_TUNE_ANALYTIC || mode > STENCIL_TUNE_MODEL ||
+        (mode == STENCIL_TUNE_MODEL && !model) || (rows && cap < 0))
+        return STENCIL_ERR_INVALID_ARG;
+    if (!stream_applicable(dtype, nx)) return STENCIL_ERR_UNSUPPORTED;
+    DevInfo *dev = nullptr;
+    int rc = device_info(&dev);
+    if (rc) return rc;
+    stencil_schedule cand[256];
+    const int nc0 = candidates(h, ny, nz, dtype, cand, 256);
+    std::vector<stencil_timing> tim;
+    std::vector<Pass> passes;
+    for (int i = 0; i < nc0; ++i) {
+        stencil_schedule r;
+        Pass ps;
+        if (resolve(h, nx, ny, nz, dtype, cand[i], *dev, r, ps)) continue;   // tile too small etc.
+        bool dup = false;   // several requested segment lengths can resolve to the same one
+        for (const auto &x : tim)
+            if (x.sched.t == r.t && x.sched.seg == r.seg && x.sched.rows_per_thread == r.rows_per_thread) dup = true;
+        if (dup) continue;
+        stencil_timing tm{};
+        tm.sched = r;
+        tm.analytic_ns_per_cell = static_cast<float>(analytic_ns(h, nx, ny, nz, dtype, r));
+        features_of(h, nx, ny, nz, dtype, r, tm.analytic_ns_per_cell, tm.features);
+        tm.ns_per_cell = -1.f;
+        tm.model_ns_per_cell = -1.f;
+        tim.push_back(tm);
+    }
+    if (tim.empty()) return STENCIL_ERR_UNSUPPORTED;
+    const int nc = static_cast<int>(tim.size());
+    if (mode == STENCIL_TUNE_MODEL) {
+        std::vector<float> X(static_cast<size_t>(nc) * STENCIL_NFEAT), y(nc);
+        for (int i = 0; i < nc; ++i) std::memcpy(&X[static_cast<size_t>(i) * STENCIL_NFEAT], tim[i].features, sizeof(tim[i].features));
+        rc = stencil_model_predict(model, X.data(), y.data(), nc);
+        if (rc) return rc;
+        for (int i = 0; i < nc; ++i) tim[i].model_ns_per_cell = std::exp(y[i]);
+    }
+    if (mode == STENCIL_TUNE_EXHAUSTIVE) {
+        const size_t bytes = static_cast<size_t>(nx * ny * nz) * elem_bytes(dtype);
+        void *a = nullptr, *b = nullptr;
+        CK(cudaMalloc(&a, bytes));
+        if (cudaMalloc(&b, bytes) != cudaSuccess) {
+            cudaFree(a);
+            return STENCIL_ERR_OOM;
+        }
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaMemset(a, 0, bytes);
+        int err = 0;
+        for (int i = 0; i < nc && !err; ++i) {
+            const int t = tim[i].sched.t;
+            const int iters = t * std::max(2, (16 + t - 1) / t);
+            err = run_impl(h, a, b, nx, ny, nz, iters, dtype, nullptr, &tim[i].sched);
+            float best = 1e30f;
+            for (int rep = 0; rep < 2 && !err; ++rep) {
+                cudaEventRecord(e0, nullptr);
+                err = run_impl(h, a, b, nx, ny, nz, iters, dtype, nullptr, &tim[i].sched);
+                cudaEventRecord(e1, nullptr);
+                if (cudaEventSynchronize(e1) != cudaSuccess) err = STENCIL_ERR_CUDA;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best = std::min(best, ms);
+            }
+            tim[i].ns_per_cell = static_cast<float>(best * 1e6 / (static_cast<double>(nx) * ny * nz * iters));
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(a);
+        cudaFree(b);
+        if (err) return err;
+    }
+    int best = 0;
+    auto key = [&](const stencil_timing &x) {
+        return mode == STENCIL_TUNE_EXHAUSTIVE ? x.ns_per_cell
+               : mode == STENCIL_TUNE_MODEL   ? x.model_ns_per_cell
+                                              : x.analytic_ns_per_cell;
+    };
+    for (int i = 1; i < nc; ++i)
+        if (key(tim[i]) < key(tim[best])) best = i;
+    *chosen = tim[best].sched;
+    if (store) {
+        bool found = false;
+        for (auto &tu : h->tuned)
+            if (tu.nx == nx && tu.ny == ny && tu.nz == nz && tu.dtype == dtype) {
+                tu.s = *chosen;
+                found = true;
+            }
+        if (!found) h->tuned.push_back({nx, ny, nz, dtype, *chosen});
+    }
+    if (rows)
+        for (int i = 0; i < nc && i < cap; ++i) rows[i] = tim[i];
+    if (nrows) *nrows = nc;
     return STENCIL_OK;
 }
 
