@@ -204,6 +204,32 @@ def case_main(args):
     return 0
 
 
+def tune_main(args):
+    """Tuner evaluation: >= 2000 measured schedule timings on seeded problems shaped like the
+    batched workload, cost model trained on 64 problems, regret on 16 held-out ones."""
+    import torch
+    from paper_2002_05983_gb300 import tune
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    res = tune.evaluate(n_train=64, n_test=16, seed=3, epochs=4000)
+
+    def stats(rows, key):
+        v = np.array([r[key] for r in rows], np.float64)
+        return {"mean": round(float(np.nanmean(v)), 4), "median": round(float(np.nanmedian(v)), 4),
+                "max": round(float(np.nanmax(v)), 4), "within_10pct": int(np.sum(v <= 0.10)), "n": int(len(v))}
+
+    out = {"tune_eval": True, "rows_total": res["rows_total"], "rows_train": res["rows_train"],
+           "train_loss": round(res["train_loss"], 5), "seconds": round(time.time() - t0, 1),
+           "regret_model_test": stats(res["test"], "regret_model"),
+           "regret_analytic_test": stats(res["test"], "regret_analytic"),
+           "regret_model_train": stats(res["train"], "regret_model"),
+           "test_problems": [dict(r["problem"], best_ns=round(r["best_ns"], 5),
+                                  regret_model=round(r["regret_model"], 4),
+                                  regret_analytic=round(r["regret_analytic"], 4)) for r in res["test"]]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,6 +237,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune-eval", action="store_true",
+                    help="measure all schedules of seeded problems, train the cost model, report regret")
     ap.add_argument("--case", default=None,
                     help="single sweep for profiling: dim:r:t:n:iters[:dtype] (grid n^dim, t=0 auto)")
     args = ap.parse_args()
@@ -218,6 +246,8 @@ def main():
         return reference_main(args)
     if args.case:
         return case_main(args)
+    if args.tune_eval:
+        return tune_main(args)
 
     import torch
     import paper_2002_05983_gb300 as st

@@ -147,8 +147,9 @@ int stencil_default_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t n
  * re-done for the GPU).  Candidates: every compiled temporal degree, several
  * stream-segment lengths and, in 3D, 2 or 4 rows per thread.
  *  - ANALYTIC: time per cell update = max(HBM bytes / bandwidth, FP32
- *    instructions incl. halo redundancy / issue rate) per pass, divided by the
- *    cell updates of the pass; no device work.
+ *    instructions incl. halo redundancy / (issue rate x an efficiency that
+ *    falls with the resident warps per SM)) per pass, divided by the cell
+ *    updates of the pass; no device work.
  *  - EXHAUSTIVE: allocates an input and output grid of the problem's size
  *    (cudaMalloc), runs each candidate for >= 16 steps after a warm-up, takes
  *    the best of two CUDA-event timings, frees the grids; synchronous.
@@ -164,9 +165,10 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
                  stencil_timing *rows, int cap, int *nrows);
 
 /* Features of (problem, schedule) for the cost model: dim, radius, log2 nx,
- * log2 ny, log2 nz, bytes per element, t, tile width (cells), tile height
- * (rows, 1 in 2D), threads per block, log2 segment length, log2 analytic ns
- * per cell update.  `sched` may be partial (0 = library choice). */
+ * log2 ny, log2 nz, bytes per element, t, resident warps per SM, tile height
+ * (rows, 1 in 2D), log2 of the unrolled loop body's FMA count
+ * ((2r+1) * t * 4 * rows * (2*dim*r+1)), log2 segment length, log2 analytic
+ * ns per cell update.  `sched` may be partial (0 = library choice). */
 int stencil_schedule_features(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
                               const stencil_schedule *sched, float *features);
 

@@ -161,6 +161,7 @@ int round_up(int a, int m) { return (a + m - 1) / m * m; }
 struct Pass {
     const void *fn = nullptr;
     int t = 0;
+    int occ = 0;   // resident blocks per SM
     dim3 grid, block;
     size_t smem = 0;
     stn::SweepArgs a{};
@@ -231,6 +232,7 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
 
     ps.fn = e->fn;
     ps.t = t;
+    ps.occ = occ;
     ps.grid = dim3(static_cast<unsigned>(tiles * nseg));
     ps.block = dim3(e->tx, e->ty);
     ps.smem = e->smem;
@@ -414,7 +416,8 @@ int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny,
 // ------------------------------------------------------------------------
 // Schedule tuner: candidates, analytic model, features.
 constexpr double kFp32InstrRate = 152.0 * 128.0 * 2.07e9;   // FP32 lane instructions / s (nominal)
-constexpr double kFpEfficiency = 0.45;                      // fraction reached by the sweep kernels
+constexpr double kFpEfficiency = 0.40;   // FMA issue share the sweep kernels reach with >= 20 warps/SM
+constexpr double kFullWarps = 20.0;      // resident warps per SM below which latency is exposed
 constexpr double kHbmBytesPerS = 6792.1e9 * 0.92;           // measured copy bandwidth, achievable share
 
 // Resolve every field of a schedule for a problem (the pass of degree t).
@@ -436,7 +439,8 @@ int resolve(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype
 }
 
 // Analytic time per cell update (ns) of a resolved schedule.
-double analytic_ns(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, const stencil_schedule &s)
+double analytic_ns(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, const stencil_schedule &s,
+                   int occ)
 {
     const int D = h->dim, R = h->r, t = s.t;
     const stn::KernelEntry *e = registry().find(D, R, t, D == 3 ? s.rows_per_thread : 1, dtype, s.threads_x,
@@ -448,16 +452,20 @@ double analytic_ns(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, in
     const double tiles = std::ceil(nx / static_cast<double>(e->cx)) * (D == 3 ? std::ceil(ny / static_cast<double>(e->cy)) : 1.0);
     const double ns_axis = D == 3 ? static_cast<double>(nz) : static_cast<double>(ny);
     const double nseg = std::ceil(ns_axis / s.seg);
-    // cell-level updates of one pass: every tile computes its thread region for
-    // every level over its segment plus the r*t stream halo
-    const double updates = tiles * nseg * bx * by * t * (s.seg + static_cast<double>(t) * R);
-    const double t_fp = updates * (2.0 * D * R + 1.0) / (kFp32InstrRate * kFpEfficiency);
+    // cell-level updates of one block: its thread region for every level over
+    // its segment plus the r*t stream halo; blocks run in waves of sms*occ
+    const double per_block = bx * by * t * (s.seg + static_cast<double>(t) * R) * (2.0 * D * R + 1.0);
+    const double slots = 152.0 * std::max(occ, 1);
+    const double waves = std::ceil(tiles * nseg / slots);
+    const double warps = static_cast<double>(occ) * e->tx * e->ty / 32.0;
+    const double eff = kFpEfficiency * std::min(1.0, warps / kFullWarps);
+    const double t_fp = waves * per_block * std::max(occ, 1) / (kFp32InstrRate / 152.0 * std::max(eff, 0.02));
     const double t_mem = N * 2.0 * es / kHbmBytesPerS;
     return std::max(t_fp, t_mem) / (N * t) * 1e9;
 }
 
 void features_of(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, const stencil_schedule &s,
-                 double analytic, float *f)
+                 int occ, double analytic, float *f)
 {
     f[0] = static_cast<float>(h->dim);
     f[1] = static_cast<float>(h->r);
@@ -466,9 +474,11 @@ void features_of(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int 
     f[4] = static_cast<float>(std::log2(static_cast<double>(nz)));
     f[5] = static_cast<float>(elem_bytes(dtype));
     f[6] = static_cast<float>(s.t);
-    f[7] = static_cast<float>(4 * s.threads_x);
-    f[8] = static_cast<float>(h->dim == 3 ? s.threads_y * s.rows_per_thread : 1);
-    f[9] = static_cast<float>(s.threads_x * s.threads_y);
+    const int vy = h->dim == 3 ? s.rows_per_thread : 1;
+    f[7] = static_cast<float>(occ * s.threads_x * s.threads_y / 32);   // resident warps per SM
+    f[8] = static_cast<float>(h->dim == 3 ? s.threads_y * vy : 1);
+    // size of the unrolled loop body: queue period x levels x cells x FMA per cell
+    f[9] = static_cast<float>(std::log2(static_cast<double>(2 * h->r + 1) * s.t * 4 * vy * (2 * h->dim * h->r + 1)));
     f[10] = static_cast<float>(std::log2(static_cast<double>(s.seg)));
     f[11] = static_cast<float>(std::log2(analytic));
 }
@@ -743,7 +753,7 @@ int stencil_schedule_features(stencil_handle h, int64_t nx, int64_t ny, int64_t 
     Pass ps;
     rc = resolve(h, nx, ny, nz, dtype, s, *dev, r, ps);
     if (rc) return rc;
-    features_of(h, nx, ny, nz, dtype, r, analytic_ns(h, nx, ny, nz, dtype, r), features);
+    features_of(h, nx, ny, nz, dtype, r, ps.occ, analytic_ns(h, nx, ny, nz, dtype, r, ps.occ), features);
     return STENCIL_OK;
 }
 
@@ -773,8 +783,8 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
         if (dup) continue;
         stencil_timing tm{};
         tm.sched = r;
-        tm.analytic_ns_per_cell = static_cast<float>(analytic_ns(h, nx, ny, nz, dtype, r));
-        features_of(h, nx, ny, nz, dtype, r, tm.analytic_ns_per_cell, tm.features);
+        tm.analytic_ns_per_cell = static_cast<float>(analytic_ns(h, nx, ny, nz, dtype, r, ps.occ));
+        features_of(h, nx, ny, nz, dtype, r, ps.occ, tm.analytic_ns_per_cell, tm.features);
         tm.ns_per_cell = -1.f;
         tm.model_ns_per_cell = -1.f;
         tim.push_back(tm);
