@@ -200,6 +200,37 @@ int stencil_model_grad(stencil_model_handle m, const float *X, const float *y, i
  * rows_per_thread; 0 if none.  */
 int stencil_max_t(int dim, int radius, int dtype, int rows_per_thread);
 
+/* One grid of a batch: `in` -> `out` (device pointers, nx*ny*nz elements of
+ * dtype), `iters` steps of the stencil of handle `h`. */
+typedef struct {
+    stencil_handle h;
+    const void *in;
+    void *out;
+    int64_t nx, ny, nz;
+    int iters;
+    int dtype;
+} stencil_batch_item;
+
+/* Sweep many independent grids of mixed dimension, radius and storage type
+ * together.  Grids are grouped by kernel class (dim, radius, dtype, temporal
+ * degree, rows per thread); each class runs as ONE persistent launch whose
+ * blocks take tiles from a device-side queue ordered pass by pass over all
+ * grids of the class, largest grids first; a tile of pass p of a grid starts
+ * only when all tiles of its pass p-1 are done (bounded wait: on expiry the
+ * device status is set, see stencil_get_device_status).  The class launches
+ * are captured once into a CUDA graph, cached for this exact item list (same
+ * pointers, sizes, handles) and replayed on `stream` by later calls.  Each
+ * grid uses its handle's tuned or default temporal degree, lowered to the
+ * largest compiled degree that divides `iters` (so every pass of a grid has
+ * the same degree); results equal stencil_run_ex with that degree bit for
+ * bit.  The batch owns one scratch grid per item (allocated on the first call
+ * for an item list, before capture) and keeps up to four cached lists.
+ * Every grid must allow the streaming kernel (rows 16-byte aligned: nx % 4
+ * FP32, nx % 8 16-bit; 16-byte aligned pointers), else STENCIL_ERR_UNSUPPORTED.
+ * Items may share a handle; `in` of one item must not overlap any `out`.
+ * Errors as stencil_run plus UNSUPPORTED. */
+int stencil_run_batched(const stencil_batch_item *items, int n, void *stream);
+
 /* Synchronise `stream`, then read and return the sticky device status of the
  * current device: STENCIL_OK, or STENCIL_ERR_TIMEOUT when a kernel gave up a
  * bounded wait (it then stopped early and its output is not valid).
@@ -210,7 +241,10 @@ int stencil_get_device_status(void *stream, int clear);
  * this handle never issue the copy of that input plane, so the wait for it
  * expires after `timeout_ms` milliseconds (1..10000), the kernel records
  * STENCIL_ERR_TIMEOUT in the device status and returns without hanging.
- * plane < 0 restores normal operation (and the default 2000 ms limit). */
+ * plane < 0 restores normal operation (and the default 2000 ms limit).
+ * In stencil_run_batched the same setting makes pass number `plane` of the
+ * grids swept with this handle never report completion, so the bounded waits
+ * of their next pass expire. */
 int stencil_set_fault_injection(stencil_handle h, int plane, int timeout_ms);
 
 /* stencil_run without any device memory allocation, for callers that cannot

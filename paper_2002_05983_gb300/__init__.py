@@ -30,7 +30,7 @@ KERNEL_AUTO, KERNEL_STREAM, KERNEL_NAIVE = 0, 1, 2
 # every symbol include/stencil.h declares
 EXPORTS = ("stencil_create", "stencil_destroy", "stencil_run", "stencil_run_ex", "stencil_run_host",
            "stencil_default_schedule", "stencil_max_t", "stencil_get_device_status",
-           "stencil_set_fault_injection", "stencil_run_noalloc", "stencil_tune",
+           "stencil_set_fault_injection", "stencil_run_noalloc", "stencil_run_batched", "stencil_tune",
            "stencil_schedule_features", "stencil_model_create", "stencil_model_destroy",
            "stencil_model_train", "stencil_model_predict", "stencil_model_normalization",
            "stencil_model_params", "stencil_model_grad", "stencil_last_cuda_error", "stencil_strerror")
@@ -54,6 +54,12 @@ class Schedule(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BatchItem(ctypes.Structure):
+    """stencil_batch_item."""
+    _fields_ = [("h", ctypes.c_void_p), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("nx", ctypes.c_int64),
+                ("ny", ctypes.c_int64), ("nz", ctypes.c_int64), ("iters", ctypes.c_int), ("dtype", ctypes.c_int)]
 
 
 class Timing(ctypes.Structure):
@@ -87,6 +93,7 @@ def _lib():
                 lib.stencil_get_device_status.argtypes = [vp, i32]
                 lib.stencil_set_fault_injection.argtypes = [vp, i32, i32]
                 lib.stencil_run_noalloc.argtypes = [vp, vp, vp, i64, i64, i64, i32, i32, vp]
+                lib.stencil_run_batched.argtypes = [ctypes.POINTER(BatchItem), i32, vp]
                 fp = ctypes.POINTER(ctypes.c_float)
                 lib.stencil_tune.argtypes = [vp, i64, i64, i64, i32, i32, vp, i32, sp,
                                              ctypes.POINTER(Timing), i32, ctypes.POINTER(i32)]
@@ -175,6 +182,12 @@ def stencil_run_noalloc(h, in_ptr, out_ptr, nx, ny, nz, iters, dtype, stream) ->
     """stencil_run without device allocation (grids up to 16 MiB); see include/stencil.h."""
     return _check(_lib().stencil_run_noalloc(h, in_ptr, out_ptr, nx, ny, nz, iters, dtype, stream),
                   "stencil_run_noalloc")
+
+
+def stencil_run_batched(items, stream) -> int:
+    """items: sequence of BatchItem (or tuples h, in_ptr, out_ptr, nx, ny, nz, iters, dtype)."""
+    arr = (BatchItem * len(items))(*[it if isinstance(it, BatchItem) else BatchItem(*it) for it in items])
+    return _check(_lib().stencil_run_batched(arr, len(items), stream), "stencil_run_batched")
 
 
 def _fptr(a):

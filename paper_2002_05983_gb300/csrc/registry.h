@@ -13,6 +13,7 @@ struct KernelEntry {
     int pf;                     // planes loaded ahead of use
     size_t smem;                // dynamic shared memory bytes
     const void *fn;             // __global__ sweep_kernel<dim, r, t, vy, S, tx, ty>
+    const void *pfn;            // __global__ sweep_persistent<dim, r, t, vy, S, tx, ty>
 };
 
 int list_2d_f32_r1(const KernelEntry **e);
@@ -47,4 +48,5 @@ int list_3d_f16_r4(const KernelEntry **e);
     {D, R, T, VY, DT, TX, TY, STN_G(D, R, T, VY, S, TX, TY)::CX, STN_G(D, R, T, VY, S, TX, TY)::CY, \
      STN_G(D, R, T, VY, S, TX, TY)::HTX, STN_G(D, R, T, VY, S, TX, TY)::HTY,                        \
      STN_G(D, R, T, VY, S, TX, TY)::PF, STN_G(D, R, T, VY, S, TX, TY)::SMEM,                        \
-     reinterpret_cast<const void *>(&stn::sweep_kernel<D, R, T, VY, S, TX, TY>)}
+     reinterpret_cast<const void *>(&stn::sweep_kernel<D, R, T, VY, S, TX, TY>),                     \
+     reinterpret_cast<const void *>(&stn::sweep_persistent<D, R, T, VY, S, TX, TY>)}

@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -40,17 +42,21 @@ namespace {
 
 thread_local int g_last_cuda_error = 0;
 
-int cuda_fail(cudaError_t e)
+// With STENCIL_DEBUG set in the environment, failing CUDA calls are reported on stderr.
+int cuda_fail(cudaError_t e, int line = 0)
 {
     g_last_cuda_error = static_cast<int>(e);
     (void)cudaGetLastError();
+    if (line && std::getenv("STENCIL_DEBUG"))
+        std::fprintf(stderr, "stencil: CUDA error %d (%s) at stencil_api.cu:%d\n", static_cast<int>(e),
+                     cudaGetErrorString(e), line);
     return e == cudaErrorMemoryAllocation ? STENCIL_ERR_OOM : STENCIL_ERR_CUDA;
 }
 
-#define CK(call)                                   \
-    do {                                           \
-        cudaError_t e_ = (call);                   \
-        if (e_ != cudaSuccess) return cuda_fail(e_); \
+#define CK(call)                                             \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, __LINE__); \
     } while (0)
 
 int elem_bytes(int dtype) { return dtype == STENCIL_F32 ? 4 : 2; }
@@ -108,7 +114,10 @@ int prepare_fn(const void *fn, int max_smem)
 {
     std::lock_guard<std::mutex> lk(g_attr_mu);
     if (std::find(g_attr_done.begin(), g_attr_done.end(), fn) != g_attr_done.end()) return 0;
-    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    cudaFuncAttributes fa;
+    CK(cudaFuncGetAttributes(&fa, fn));   // static shared memory counts against the same limit
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            max_smem - static_cast<int>(fa.sharedSizeBytes)));
     g_attr_done.push_back(fn);
     return 0;
 }
@@ -270,6 +279,10 @@ int encode_map(CUtensorMap *m, const void *ptr, int64_t nx, int64_t ny, int64_t 
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         g_last_cuda_error = static_cast<int>(r);
+        if (std::getenv("STENCIL_DEBUG"))
+            std::fprintf(stderr, "stencil: cuTensorMapEncodeTiled error %d (box %d x %d, dims %lld %lld %lld)\n",
+                         static_cast<int>(r), box_w, box_h, static_cast<long long>(nx), static_cast<long long>(ny),
+                         static_cast<long long>(nz));
         return STENCIL_ERR_CUDA;
     }
     return 0;
@@ -291,6 +304,12 @@ int ensure_scratch(stencil_plan *h, size_t bytes)
         h->scratch_dev = dev;
     }
     return 0;
+}
+
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
 }
 
 bool overlap(const void *a, const void *b, size_t n)
@@ -507,6 +526,204 @@ int candidates(const stencil_plan *h, int64_t ny, int64_t nz, int dtype, stencil
             }
     }
     return n;
+}
+
+// ------------------------------------------------------------------------
+// Batched persistent sweeps: plans, device task tables and cached CUDA graphs.
+struct BatchClass {
+    const void *pfn = nullptr;
+    dim3 grid, block;
+    size_t smem = 0;
+    stn::BatchArgs args{};
+    void *dev_args = nullptr, *dev_maps = nullptr, *dev_tasks = nullptr, *dev_done = nullptr;
+};
+
+struct BatchEntry {
+    std::vector<char> key;
+    std::vector<void *> scratch;   // one per item (null when a grid needs a single pass)
+    std::vector<BatchClass> classes;
+    cudaGraphExec_t exec = nullptr;
+    int dev = -1;
+};
+
+std::mutex g_batch_mu;
+std::vector<BatchEntry *> g_batch;   // most recent last
+
+void free_entry(BatchEntry *e)
+{
+    cudaDeviceSynchronize();   // a replay may still use the tables
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    for (void *p : e->scratch)
+        if (p) cudaFree(p);
+    for (auto &c : e->classes) {
+        for (void *p : {c.dev_args, c.dev_maps, c.dev_tasks, c.dev_done})
+            if (p) cudaFree(p);
+    }
+    delete e;
+}
+
+std::vector<char> batch_key(const stencil_batch_item *items, int n, int dev)
+{
+    std::vector<char> k(sizeof(int) + sizeof(stencil_batch_item) * n);
+    std::memcpy(k.data(), &dev, sizeof(int));
+    std::memcpy(k.data() + sizeof(int), items, sizeof(stencil_batch_item) * n);
+    for (int i = 0; i < n; ++i) {   // the handles' coefficients, schedules and test settings
+        const stencil_plan *h = items[i].h;
+        const char *c = reinterpret_cast<const char *>(h->c);
+        k.insert(k.end(), c, c + sizeof(float) * h->K);
+        int extra[2] = {h->fault_plane, h->timeout_ms};
+        k.insert(k.end(), reinterpret_cast<char *>(extra), reinterpret_cast<char *>(extra) + sizeof(extra));
+        for (const auto &tu : h->tuned) {
+            const char *b = reinterpret_cast<const char *>(&tu);
+            k.insert(k.end(), b, b + sizeof(tu));
+        }
+    }
+    return k;
+}
+
+int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cudaStream_t st, BatchEntry *E)
+{
+    struct Item {
+        int idx, L, t;
+        Pass ps;
+        const stn::KernelEntry *e;
+        int rows;
+    };
+    std::vector<Item> it;
+    for (int i = 0; i < n; ++i) {
+        const stencil_batch_item &b = items[i];
+        stencil_plan *h = b.h;
+        stencil_schedule s;
+        default_schedule(h, b.nx, b.ny, b.nz, b.dtype, &s);
+        for (const auto &tu : h->tuned)
+            if (tu.nx == b.nx && tu.ny == b.ny && tu.nz == b.nz && tu.dtype == b.dtype) s = tu.s;
+        if (s.kernel != STENCIL_KERNEL_STREAM) return STENCIL_ERR_UNSUPPORTED;
+        // largest compiled degree <= the chosen one that divides iters
+        int t = std::max(1, std::min(s.t, b.iters));
+        while (t > 1 && (b.iters % t != 0 || !registry().find(h->dim, h->r, t, h->dim == 3 ? s.rows_per_thread : 1,
+                                                                b.dtype, s.threads_x, s.threads_y)))
+            --t;
+        s.t = t;
+        Item x;
+        x.idx = i;
+        x.t = t;
+        x.L = b.iters / t;
+        x.rows = h->dim == 3 ? s.rows_per_thread : 1;
+        int rc = plan_pass(h, b.nx, b.ny, b.nz, b.dtype, t, s, dev, x.ps);
+        if (rc) return rc;
+        x.e = registry().find(h->dim, h->r, t, x.rows, b.dtype, s.threads_x, s.threads_y);
+        if (!x.e) return STENCIL_ERR_UNSUPPORTED;
+        x.ps.a.timeout_ms = h->timeout_ms;
+        it.push_back(x);
+    }
+    // scratch grids
+    E->scratch.assign(n, nullptr);
+    for (const Item &x : it)
+        if (x.L > 1) {
+            const stencil_batch_item &b = items[x.idx];
+            const size_t bytes = static_cast<size_t>(b.nx * b.ny * b.nz) * elem_bytes(b.dtype);
+            CK(cudaMalloc(&E->scratch[x.idx], bytes));
+        }
+    // group by kernel class, largest grids first inside a class
+    std::vector<const stn::KernelEntry *> kinds;
+    for (const Item &x : it)
+        if (std::find(kinds.begin(), kinds.end(), x.e) == kinds.end()) kinds.push_back(x.e);
+    for (const stn::KernelEntry *kind : kinds) {
+        std::vector<const Item *> mine;
+        for (const Item &x : it)
+            if (x.e == kind) mine.push_back(&x);
+        std::sort(mine.begin(), mine.end(), [](const Item *a, const Item *b) { return a->ps.grid.x > b->ps.grid.x; });
+        int maxL = 0;
+        for (const Item *x : mine) maxL = std::max(maxL, x->L);
+        std::vector<stn::SweepArgs> args;
+        std::vector<CUtensorMap> maps;
+        std::vector<stn::BatchTask> tasks;
+        std::vector<int> last_task(n, -1);
+        int total = 0, fault_task = -1, timeout = 2000;
+        for (int p = 0; p < maxL; ++p)
+            for (const Item *x : mine) {
+                if (p >= x->L) continue;
+                const stencil_batch_item &b = items[x->idx];
+                void *scr = E->scratch[x->idx];
+                const void *src = p == 0 ? b.in : ((x->L - p) % 2 == 0 ? b.out : scr);
+                void *dst = ((x->L - 1 - p) % 2 == 0) ? b.out : scr;
+                stn::SweepArgs a = x->ps.a;
+                a.in = src;
+                a.out = dst;
+                args.push_back(a);
+                CUtensorMap m;
+                std::memset(&m, 0, sizeof(m));
+                if (b.h->dim == 3) {
+                    const int pad = b.dtype == STENCIL_F32 ? 4 : 8;
+                    int rc = encode_map(&m, src, b.nx, b.ny, b.nz, b.dtype, 4 * kind->tx + 2 * pad,
+                                        kind->ty * x->rows + 2 * b.h->r);
+                    if (rc) return rc;
+                }
+                maps.push_back(m);
+                stn::BatchTask tk;
+                tk.prev = last_task[x->idx];
+                tk.ntiles = static_cast<int>(x->ps.grid.x);
+                tk.first = total;
+                total += tk.ntiles;
+                if (b.h->fault_plane == p && fault_task < 0) fault_task = static_cast<int>(tasks.size());
+                timeout = b.h->timeout_ms;
+                last_task[x->idx] = static_cast<int>(tasks.size());
+                tasks.push_back(tk);
+            }
+        BatchClass c;
+        c.pfn = kind->pfn;
+        c.block = dim3(kind->tx, kind->ty);
+        c.smem = kind->smem;
+        int rc = prepare_fn(c.pfn, dev.max_smem);
+        if (rc) return rc;
+        int occ = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.pfn, kind->tx * kind->ty, kind->smem));
+        if (occ < 1) return STENCIL_ERR_UNSUPPORTED;
+        c.grid = dim3(static_cast<unsigned>(std::min<int64_t>(total, static_cast<int64_t>(dev.sms) * occ)));
+        const int nt = static_cast<int>(tasks.size());
+        CK(cudaMalloc(&c.dev_args, sizeof(stn::SweepArgs) * nt));
+        CK(cudaMalloc(&c.dev_maps, sizeof(CUtensorMap) * nt));
+        CK(cudaMalloc(&c.dev_tasks, sizeof(stn::BatchTask) * nt));
+        CK(cudaMalloc(&c.dev_done, sizeof(int) * (nt + 1)));
+        CK(cudaMemcpy(c.dev_args, args.data(), sizeof(stn::SweepArgs) * nt, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c.dev_maps, maps.data(), sizeof(CUtensorMap) * nt, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c.dev_tasks, tasks.data(), sizeof(stn::BatchTask) * nt, cudaMemcpyHostToDevice));
+        stn::BatchArgs &B = c.args;
+        B.args = static_cast<const stn::SweepArgs *>(c.dev_args);
+        B.maps = static_cast<const CUtensorMap *>(c.dev_maps);
+        B.tasks = static_cast<const stn::BatchTask *>(c.dev_tasks);
+        B.done = static_cast<int *>(c.dev_done);
+        B.head = static_cast<int *>(c.dev_done) + nt;
+        B.status = dev.status;
+        B.ntasks = nt;
+        B.total = total;
+        B.timeout_ms = timeout;
+        B.fault_task = fault_task;
+        E->classes.push_back(c);
+    }
+    // one CUDA graph: per class, reset its counters and run its persistent launch.  It is
+    // captured on a private stream (the caller's may be the legacy stream, which cannot be
+    // captured) and launched on the caller's stream.
+    (void)st;
+    cudaStream_t cap = nullptr;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+        for (auto &c : E->classes) {
+            if (err == cudaSuccess)
+                err = cudaMemsetAsync(c.dev_done, 0, sizeof(int) * (c.args.ntasks + 1), cap);
+            void *args[] = {&c.args};
+            if (err == cudaSuccess) err = cudaLaunchKernel(c.pfn, c.grid, c.block, args, c.smem, cap);
+        }
+        const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (err == cudaSuccess) err = e2;
+    }
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&E->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    if (err != cudaSuccess) return cuda_fail(err, __LINE__);
+    return 0;
 }
 
 // ------------------------------------------------------------------------
@@ -729,6 +946,61 @@ int stencil_run_noalloc(stencil_handle h, const void *in, void *out, int64_t nx,
         }
         src = dst;
     }
+    return STENCIL_OK;
+}
+
+int stencil_run_batched(const stencil_batch_item *items, int n, void *stream)
+{
+    if (!items || n < 1) return STENCIL_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        const stencil_batch_item &b = items[i];
+        int rc = check_problem(b.h, b.in, b.out, b.nx, b.ny, b.nz, b.iters, b.dtype);
+        if (rc) return rc;
+        if (b.iters < 1) return STENCIL_ERR_INVALID_ARG;
+        const bool aligned = (reinterpret_cast<uintptr_t>(b.in) | reinterpret_cast<uintptr_t>(b.out)) % 16 == 0;
+        if (!stream_applicable(b.dtype, b.nx) || !aligned) return STENCIL_ERR_UNSUPPORTED;
+        const size_t bi = static_cast<size_t>(b.nx * b.ny * b.nz) * elem_bytes(b.dtype);
+        for (int j = 0; j < n; ++j) {   // no input or output may overlap another item's output
+            if (j == i) continue;
+            const stencil_batch_item &c = items[j];
+            const size_t bj = static_cast<size_t>(c.nx * c.ny * c.nz) * elem_bytes(c.dtype);
+            if (ranges_overlap(b.out, bi, c.out, bj) || ranges_overlap(b.in, bi, c.out, bj))
+                return STENCIL_ERR_ALIAS;
+        }
+    }
+    DevInfo *dev = nullptr;
+    int rc = device_info(&dev);
+    if (rc) return rc;
+    int devno = 0;
+    CK(cudaGetDevice(&devno));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    const std::vector<char> key = batch_key(items, n, devno);
+    BatchEntry *E = nullptr;
+    for (size_t i = 0; i < g_batch.size(); ++i)
+        if (g_batch[i]->key == key) {
+            E = g_batch[i];
+            g_batch.erase(g_batch.begin() + static_cast<long>(i));
+            g_batch.push_back(E);
+            break;
+        }
+    if (!E) {
+        E = new (std::nothrow) BatchEntry;
+        if (!E) return STENCIL_ERR_OOM;
+        E->key = key;
+        E->dev = devno;
+        rc = build_batch(items, n, *dev, st, E);
+        if (rc) {
+            free_entry(E);
+            return rc;
+        }
+        g_batch.push_back(E);
+        while (g_batch.size() > 4) {
+            free_entry(g_batch.front());
+            g_batch.erase(g_batch.begin());
+        }
+    }
+    CK(cudaGraphLaunch(E->exec, st));
     return STENCIL_OK;
 }
 

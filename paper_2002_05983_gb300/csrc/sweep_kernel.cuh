@@ -285,10 +285,19 @@ __device__ __forceinline__ void ghost_fill(float *plane, const Ghost &g, int pw,
     }
 }
 
-// ------------------------------------------------------------------ kernel
+__device__ __forceinline__ void mbar_inval(uint32_t bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// ------------------------------------------------------------------ one tile
+// One x (and y) tile and stream segment of one pass, by one thread block.
+// `tile` indexes tile_x + ntx * (tile_y + nty * segment).  Returns false if a
+// bounded wait expired (the device status word is then set).  Leaves the
+// block's shared memory free for the next tile.
 template <int D, int R, int T, int VY, typename S, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY)
-    sweep_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ SweepArgs a)
+__device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepArgs &a, int tile,
+                                           unsigned char *smem)
 {
     using G = Geo<D, R, T, VY, static_cast<int>(sizeof(S)), TX, TY>;
     static_assert(D == 2 || D == 3, "dim");
@@ -304,7 +313,6 @@ __global__ void __launch_bounds__(TX *TY)
     constexpr int DEPTH = G::DEPTH;
     constexpr int SLOT32 = G::SLOT32, SLOTIN = G::SLOTIN;
 
-    extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     volatile int *sflag = reinterpret_cast<volatile int *>(smem + 8 * kMaxDepthIn);
     S *ring_in = reinterpret_cast<S *>(smem + kSmemHeader);
@@ -318,7 +326,7 @@ __global__ void __launch_bounds__(TX *TY)
     const int tid = ty * TX + tx;
 
     // ---- tile and segment of this block
-    int b = blockIdx.x;
+    int b = tile;
     const int tile_x = b % a.ntx;
     b /= a.ntx;
     int tile_y = 0;
@@ -421,7 +429,7 @@ __global__ void __launch_bounds__(TX *TY)
                           static_cast<const S *>(a.in) + static_cast<int64_t>(q) * a.nx + xa, bytes, bar);
         } else {
             mbar_arrive_expect_tx(bar, static_cast<uint32_t>(PWIN * G::PH * sizeof(S)));
-            tma_load_3d(smem_addr(dst), &tmap, ox_in, oy, q, bar);
+            tma_load_3d(smem_addr(dst), tmap, ox_in, oy, q, bar);
         }
     };
     if (tid == 0) {
@@ -668,6 +676,113 @@ __global__ void __launch_bounds__(TX *TY)
             mbar_wait_bounded(smem_addr(bars + qq % DEPTH), static_cast<uint32_t>((qq / DEPTH - lap0) & 1),
                               a.timeout_ms);
         }
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int i = 0; i < DEPTH; ++i) mbar_inval(smem_addr(bars + i));
+    __syncthreads();
+    return !aborted;
+}
+
+// ------------------------------------------------------------------ kernels
+// One pass over the grid: block b sweeps tile b.
+template <int D, int R, int T, int VY, typename S, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY)
+    sweep_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ SweepArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    sweep_tile<D, R, T, VY, S, TX, TY>(&tmap, a, static_cast<int>(blockIdx.x), smem);
+}
+
+// Persistent sweep of many grids of one kernel class, all passes, from a device tile
+// queue.  Queue order is pass-major over the grids, so every tile a block waits for was
+// taken earlier by a running block: pass p of grid g starts a tile only after all tiles
+// of its pass p-1 are counted done (bounded spin; on expiry the status word is set and
+// the block stops).
+struct BatchTask {
+    int prev;             // task whose output this task reads (-1 for a grid's first pass)
+    int ntiles;           // tiles of this task
+    int first;            // queue index of its first tile
+};
+
+struct BatchArgs {
+    const SweepArgs *args;      // per task
+    const CUtensorMap *maps;    // per task (3D)
+    const BatchTask *tasks;
+    int *done;                  // per task: tiles finished
+    int *head;                  // next queue index
+    unsigned *status;
+    int ntasks, total;          // tasks, queue length
+    int timeout_ms;
+    int fault_task;             // test hook: this task never reports its tiles done (< 0: off)
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+template <int D, int R, int T, int VY, typename S, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY)
+    sweep_persistent(const __grid_constant__ BatchArgs B)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ int s_q, s_ok;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    for (;;) {
+        if (tid == 0) s_q = atomicAdd(B.head, 1);
+        __syncthreads();
+        const int q = s_q;
+        if (q >= B.total) break;
+        // task of queue index q (binary search on first-tile indices)
+        int lo = 0, hi = B.ntasks - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (B.tasks[mid].first <= q) lo = mid;
+            else hi = mid - 1;
+        }
+        const int task = lo;
+        const BatchTask tk = B.tasks[task];
+        if (tid == 0) {
+            int ok = 1;
+            if (tk.prev >= 0) {
+                const int need = B.tasks[tk.prev].ntiles;
+                const int *cnt = B.done + tk.prev;
+                if (ld_acquire(cnt) < need) {
+                    const uint64_t t0 = global_ns();
+                    const uint64_t lim = static_cast<uint64_t>(B.timeout_ms) * 1000000ull;
+                    while (ld_acquire(cnt) < need) {
+                        if (global_ns() - t0 > lim) {
+                            ok = 0;
+                            atomicOr(B.status, kStatusTimeout);
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                }
+                // the input was written by other blocks' generic stores; the tile reads it with TMA
+                fence_proxy_async_global();
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        const SweepArgs a = B.args[task];
+        const bool done = sweep_tile<D, R, T, VY, S, TX, TY>(D == 3 ? B.maps + task : nullptr, a, q - tk.first, smem);
+        __syncthreads();
+        if (tid == 0 && task != B.fault_task) {
+            __threadfence();
+            fence_proxy_async_global();
+            atomicAdd(B.done + task, 1);
+        }
+        if (!done) break;
     }
 }
 
