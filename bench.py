@@ -204,6 +204,151 @@ def case_main(args):
     return 0
 
 
+def _timed(fn, reps=2):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return best
+
+
+def _rand(shape, dtype, seed):
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    return torch.rand(shape, device="cuda", generator=g).to(dtype)
+
+
+def _row(**kw):
+    print(json.dumps(kw), flush=True)
+
+
+def suite_main(args):
+    """Measurements of the other workloads.  Timing grids are torch.rand on the device (values do
+    not change the speed); parity and error figures use the seeded workload inputs."""
+    import torch
+    import oracle
+    import paper_2002_05983_gb300 as st
+    from paper_2002_05983_gb300 import metrics
+    torch.cuda.set_device(0)
+    pk = peaks()
+    f32 = torch.float32
+
+    def roof(dim, r, t, es):
+        return metrics.roofline_cells(dim, r, t, es, pk["fp32_flops"], pk["hbm_gbs"] * 1e9) / 1e9
+
+    if args.suite in ("sweep2d", "sweep3d"):
+        dim = 2 if args.suite == "sweep2d" else 3
+        shape, iters = ((16384, 16384), 1000) if dim == 2 else ((512, 512, 512), 200)
+        x = _rand(shape, f32, 0)
+        out = torch.empty_like(x)
+        n = x.numel()
+        for r in RADII:
+            s = st.Stencil(dim, r, gen.coefficients(dim, r))
+            for vy in ((1,) if dim == 2 else (2, 4)):
+                for t in range(1, st.stencil_max_t(dim, r, 0, vy) + 1):
+                    sc = st.schedule(kernel=st.KERNEL_STREAM, t=t, rows_per_thread=vy)
+                    sec = _timed(lambda: s.run(x, iters, out=out, sched=sc), reps=1)
+                    g = n * iters / sec / 1e9
+                    _row(suite=args.suite, dim=dim, r=r, t=t, rows_per_thread=vy, iters=iters, grid=list(shape),
+                         gcells=round(g, 1), gflops=round(g * metrics.flop_per_cell(dim, r), 1),
+                         roofline_gcells=round(roof(dim, r, t, 4), 1), roofline_frac=round(g / roof(dim, r, t, 4), 4))
+            sec = _timed(lambda: s.run(x, iters, out=out), reps=1)
+            d = s.default_schedule(shape)
+            _row(suite=args.suite, dim=dim, r=r, default_t=d.t, default_rows=d.rows_per_thread,
+                 gcells_default=round(n * iters / sec / 1e9, 1))
+        # parity on the seeded crop at the full step count (clamp at the crop's own edges)
+        side = 1024 if dim == 2 else 128
+        f = crop_input(side) if dim == 2 else gen.workload_grid(3, side, side, side)
+        for r in RADII:
+            c = gen.coefficients(dim, r)
+            s = st.Stencil(dim, r, c)
+            got = s.run(torch.from_numpy(f).cuda(), iters).cpu().numpy()
+            w32 = oracle.sweep_f32(f, dim, r, c, iters)
+            w64 = oracle.sweep_f64(f.astype(np.float64), dim, r, c.astype(np.float64), iters)
+            _row(suite=args.suite, parity=True, dim=dim, r=r, crop=side, iters=iters,
+                 bit_exact_vs_fp32_oracle=bool(np.array_equal(got, w32)),
+                 max_abs_vs_fp64=float(np.max(np.abs(got - w64))), bound=2e-6 * iters)
+        return 0
+
+    if args.suite == "precision":
+        iters = 500
+        for dim, shape, small in ((3, (768, 768, 768), 128), (2, (32768, 32768), 2048)):
+            r = 4
+            s = st.Stencil(dim, r, gen.coefficients(dim, r))
+            base = None
+            for name, dt, es in (("f32", torch.float32, 4), ("bf16", torch.bfloat16, 2), ("f16", torch.float16, 2)):
+                x = _rand(shape, dt, 1)
+                out = torch.empty_like(x)
+                sec = _timed(lambda: s.run(x, iters, out=out), reps=1)
+                g = x.numel() * iters / sec / 1e9
+                base = base or g
+                t = s.default_schedule(shape, st.dtype_code(x)).t
+                _row(suite="precision", dim=dim, r=r, dtype=name, grid=list(shape), iters=iters, t=t,
+                     gcells=round(g, 1), speedup_vs_f32=round(g / base, 3),
+                     roofline_frac=round(g / roof(dim, r, t, es), 4))
+                del x, out
+                torch.cuda.empty_cache()
+            # accuracy on the small instance, 500 steps, against the FP64 oracle
+            f = gen.workload_grid(dim, *((small,) * dim))
+            c = gen.coefficients(dim, r)
+            w64 = oracle.sweep_f64(f.astype(np.float64), dim, r, c.astype(np.float64), iters)
+            for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float16)):
+                xs = torch.from_numpy(f).to(dt)
+                got = s.run(xs.cuda(), iters).float().cpu().numpy().astype(np.float64)
+                w_in = oracle.sweep_f64(xs.float().numpy().astype(np.float64), dim, r, c.astype(np.float64), iters)
+                _row(suite="precision", accuracy=True, dim=dim, r=r, dtype=name, grid=[small] * dim, iters=iters,
+                     max_abs=float(np.max(np.abs(got - w64))),
+                     rel_l2=float(np.linalg.norm(got - w64) / np.linalg.norm(w64)),
+                     max_abs_vs_rounded_input=float(np.max(np.abs(got - w_in))),
+                     rel_l2_vs_rounded_input=float(np.linalg.norm(got - w_in) / np.linalg.norm(w_in)))
+        return 0
+
+    if args.suite == "batch":
+        iters = 100
+        items = gen.batch_list()
+        for it in items:   # rows must be 16-byte aligned for the streaming kernel
+            it["nx"] -= it["nx"] % 8
+        stencils, bufs, batch = {}, [], []
+        for k, it in enumerate(items):
+            key = (it["dim"], it["r"])
+            if key not in stencils:
+                stencils[key] = st.Stencil(it["dim"], it["r"], gen.coefficients(*key))
+            shape = (it["ny"], it["nx"]) if it["dim"] == 2 else (it["nz"], it["ny"], it["nx"])
+            dt = torch.bfloat16 if it["dtype"] == "bf16" else torch.float32
+            x = _rand(shape, dt, 100 + k)
+            y = torch.empty_like(x)
+            bufs.append((x, y))
+            batch.append((stencils[key].handle, x.data_ptr(), y.data_ptr(), it["nx"], it["ny"], it["nz"], iters,
+                          st.dtype_code(x)))
+        stream = torch.cuda.current_stream().cuda_stream
+        cells = sum(b[3] * b[4] * b[5] for b in batch) * iters
+
+        def singles():
+            for (h, xp, yp, nx, ny, nz, it_, code), (x, y) in zip(batch, bufs):
+                st.stencil_run(h, xp, yp, nx, ny, nz, it_, code, stream)
+
+        t_single = _timed(singles, reps=2)
+        ref = [y.clone() for _, y in bufs]
+        t_batch = _timed(lambda: st.stencil_run_batched(batch, stream), reps=3)
+        assert st.stencil_get_device_status() == 0
+        same = sum(int(torch.equal(y, r)) for (x, y), r, it in zip(bufs, ref, items) if it["dtype"] == "f32")
+        n32 = sum(1 for it in items if it["dtype"] == "f32")
+        _row(suite="batch", grids=len(batch), grids_2d=sum(1 for it in items if it["dim"] == 2), iters=iters,
+             cell_updates=cells, seconds_individual=round(t_single, 4), seconds_batched=round(t_batch, 4),
+             gcells_individual=round(cells / t_single / 1e9, 1), gcells_batched=round(cells / t_batch / 1e9, 1),
+             speedup=round(t_single / t_batch, 3), fp32_grids_bit_identical_to_individual=f"{same}/{n32}")
+        return 0
+    return 1
+
+
 def tune_main(args):
     """Tuner evaluation: >= 2000 measured schedule timings on seeded problems shaped like the
     batched workload, cost model trained on 64 problems, regret on 16 held-out ones."""
@@ -237,6 +382,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--suite", choices=["sweep2d", "sweep3d", "precision", "batch"], default=None,
+                    help="other workloads: t sweeps, 16-bit storage, 96-grid batch (JSON lines)")
     ap.add_argument("--tune-eval", action="store_true",
                     help="measure all schedules of seeded problems, train the cost model, report regret")
     ap.add_argument("--case", default=None,
@@ -248,6 +395,8 @@ def main():
         return case_main(args)
     if args.tune_eval:
         return tune_main(args)
+    if args.suite:
+        return suite_main(args)
 
     import torch
     import paper_2002_05983_gb300 as st
