@@ -31,11 +31,11 @@ template <int D, int R, int T, int VY, int ES, int TX, int TY> struct Geo {
     static constexpr int SLOT32 = rup(PW * PH, 32);    // floats per FP32 ring slot
     static constexpr int SLOTIN = rup(PWIN * PH * ES, 128) / ES;   // elements per input slot
     static constexpr int PFMIN = (D == 2) ? 4 : 2;
-    static constexpr int LAG1 = F32S ? R : R + 1;      // steps level 1 trails the input
-    static constexpr int KEEP = F32S ? R + 1 : 1;      // input slots held besides prefetch
+    static constexpr int LAG1 = R;                     // steps level 1 trails the input
+    static constexpr int KEEP = R + 1;                 // input slots held besides prefetch
     static constexpr int DEPTH = QP * cdiv(KEEP + PFMIN, QP);   // input ring slots
     static constexpr int PF = DEPTH - KEEP;            // planes loaded ahead of use
-    static constexpr int NRING = F32S ? T - 1 : T;     // FP32 rings written by the levels
+    static constexpr int NRING = T - 1;                // FP32 rings written by levels 1..T-1
     static constexpr size_t SMEM = static_cast<size_t>(kSmemHeader) +
                                    static_cast<size_t>(DEPTH) * SLOTIN * ES +
                                    static_cast<size_t>(NRING) * QP * SLOT32 * 4;

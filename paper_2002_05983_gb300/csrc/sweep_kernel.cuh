@@ -8,16 +8,19 @@
 // along z) and a segment of the streaming axis.  Each step of the block's
 // loop advances every time level by one plane:
 //   * level 0 is the input: planes arrive by TMA (1D bulk copies of a row in
-//     2D, a 3D tensor-map box in 3D) into a ring of shared-memory slots with
-//     one mbarrier per slot, `prefetch` planes ahead of use;
-//   * level s (1..T) computes plane p_s = k - s*(r+1) from level s-1: the
-//     streaming-axis neighbours come from a register queue of 2r+1 planes of
-//     the thread's own cells, the in-plane neighbours from level s-1's FP32
-//     shared-memory ring of r+2 planes.  The lag of r+1 planes between levels
-//     means everything a level reads was written in an earlier step, so one
-//     __syncthreads per step orders all of it, and levels are evaluated from
-//     T down to 1 so that a level reads its input queue before the level
-//     below overwrites the oldest plane of it;
+//     2D, a 3D tensor-map box in 3D) into a ring of shared-memory slots in
+//     the storage type (FP32, BF16 or FP16) with one mbarrier per slot,
+//     `prefetch` planes ahead of use;
+//   * level s (1..T) computes plane k - lag(s), lag(s) = r + (s-1)*(r+1),
+//     from level s-1: the streaming-axis neighbours come from a register
+//     queue of 2r+1 planes of the thread's own cells, the in-plane
+//     neighbours from shared memory (level 1 from the input ring, widened to
+//     FP32 on load, which is exact; higher levels from FP32 rings of 2r+1
+//     planes).  Everything a level reads in shared memory was written at
+//     least one step earlier and is overwritten at least one step after its
+//     last read, so one __syncthreads per step orders all of it; levels run
+//     from T down to 2, then 0, then 1, so a level reads its register queue
+//     before the level below overwrites the oldest plane of it;
 //   * level T writes the compute tile of its plane to global memory.
 // The FP32 arithmetic of every cell is one multiply and 2*D*r fused
 // multiply-adds in the order centre, then for i = 1..r: W, E, S, N[, B, A]
@@ -213,7 +216,7 @@ __host__ __device__ constexpr int cclamp(int a, int lo, int hi) { return a < lo 
 
 // ------------------------------------------------------- ghost (clamp) fill
 // Tasks that overwrite the out-of-grid frame (width <= 4 in x, r in y) of a
-// padded FP32 plane with clamped border values; float4 granularity.
+// padded plane with clamped border values, in groups of four cells.
 struct Ghost {
     int ntask, nA, nc;      // total tasks, column tasks, columns per in-grid row (0..2)
     int rA0;                // first in-grid padded row
@@ -251,18 +254,30 @@ __device__ __forceinline__ Ghost make_ghost(int ox, int oy, int pw, int ph, int 
     return g;
 }
 
-__device__ __forceinline__ void ghost_fill(float *plane, const Ghost &g, int pw, int ox, int nx,
-                                           int tid, int nthr)
+// Cells are moved as raw bits, four at a time: 4-byte cells (FP32 rings, FP32
+// input) or 2-byte cells (BF16/FP16 input).
+template <int ES>
+__device__ __forceinline__ void ghost_fill(void *plane_, const Ghost &g, int pw, int ox, int nx, int tid, int nthr)
 {
+    using W = typename std::conditional<ES == 4, uint32_t, uint16_t>::type;
+    using V = typename std::conditional<ES == 4, uint4, uint2>::type;
+    W *plane = static_cast<W *>(plane_);
+    auto bcast = [](W e) -> V {
+        if constexpr (ES == 4) {
+            return make_uint4(e, e, e, e);
+        } else {
+            const uint32_t u = static_cast<uint32_t>(e) | (static_cast<uint32_t>(e) << 16);
+            return make_uint2(u, u);
+        }
+    };
     for (int t = tid; t < g.ntask; t += nthr) {
         int row, col;
-        float4 v;
+        V v;
         if (t < g.nA) {
             row = g.rA0 + t / g.nc;
             const bool left = (t % g.nc == 0) && g.cL >= 0;
             col = left ? g.cL : g.cR;
-            const float s = plane[row * pw + (left ? g.srcL : g.srcR)];
-            v = make_float4(s, s, s, s);
+            v = bcast(plane[row * pw + (left ? g.srcL : g.srcR)]);
         } else {
             const int u = t - g.nA;
             const int gr = u / g.ncg;
@@ -271,17 +286,11 @@ __device__ __forceinline__ void ghost_fill(float *plane, const Ghost &g, int pw,
             if (gr < g.nT) { row = g.rT0 + gr; srow = g.srcT; }
             else { row = g.rB0 + gr - g.nT; srow = g.srcB; }
             const int x4 = ox + 4 * col;
-            if (x4 < 0) {
-                const float s = plane[srow * pw + g.srcL];
-                v = make_float4(s, s, s, s);
-            } else if (x4 >= nx) {
-                const float s = plane[srow * pw + g.srcR];
-                v = make_float4(s, s, s, s);
-            } else {
-                v = *reinterpret_cast<const float4 *>(plane + srow * pw + 4 * col);
-            }
+            if (x4 < 0) v = bcast(plane[srow * pw + g.srcL]);
+            else if (x4 >= nx) v = bcast(plane[srow * pw + g.srcR]);
+            else v = *reinterpret_cast<const V *>(plane + srow * pw + 4 * col);
         }
-        *reinterpret_cast<float4 *>(plane + row * pw + 4 * col) = v;
+        *reinterpret_cast<V *>(plane + row * pw + 4 * col) = v;
     }
 }
 
@@ -317,10 +326,8 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     volatile int *sflag = reinterpret_cast<volatile int *>(smem + 8 * kMaxDepthIn);
     S *ring_in = reinterpret_cast<S *>(smem + kSmemHeader);
     float *rings = reinterpret_cast<float *>(smem + kSmemHeader + DEPTH * SLOTIN * sizeof(S));
-    // FP32 ring of level s (F32S: levels 1..T-1, else 0..T-1), slot j = plane mod QP
-    auto ring32 = [&](int s, int j) -> float * {
-        return rings + ((F32S ? s - 1 : s) * QP + j) * SLOT32;
-    };
+    // FP32 ring of level s (1..T-1), slot j = plane mod QP; level 0 is the input ring
+    auto ring32 = [&](int s, int j) -> float * { return rings + ((s - 1) * QP + j) * SLOT32; };
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
@@ -401,7 +408,8 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     const int lmax = min(hi[0], last);                 // last input plane to load
     const int lap0 = k0 / DEPTH;
 
-    const Ghost gh = make_ghost(ox, oy, PW, G::PH, a.nx, (D == 3) ? a.ny : 1, R);
+    const Ghost gh = make_ghost(ox, oy, PW, G::PH, a.nx, (D == 3) ? a.ny : 1, R);   // FP32 rings
+    const Ghost gh_in = F32S ? gh : make_ghost(ox_in, oy, PWIN, G::PH, a.nx, (D == 3) ? a.ny : 1, R);
 
     if (tid == 0) {
         for (int i = 0; i < DEPTH; ++i) mbar_init(smem_addr(bars + i), 1);
@@ -478,30 +486,36 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                 return;
             }
         }
-        // level s-1's plane p in shared memory, at this thread's cell 0
-        const float *own;
-        if constexpr (F32S && s == 1) {
+        // level s-1's plane p in shared memory at this thread's cell 0: level 1 reads the
+        // input ring (storage type, widened exactly on load), higher levels the FP32 rings
+        const S *own_in = nullptr;
+        const float *own32 = nullptr;
+        if constexpr (s == 1) {
             constexpr int d = J - R;    // input slot of plane k-R relative to plane kb
-            own = reinterpret_cast<const float *>(d >= 0 ? inb + d * SLOTIN : inbp + (d + QP) * SLOTIN);
+            own_in = d >= 0 ? inb + d * SLOTIN : inbp + (d + QP) * SLOTIN;
         } else {
-            own = ring32(s - 1, js) + toff;
+            own32 = ring32(s - 1, js) + toff;
         }
+        auto ld = [&](int row, int dx, float (&v)[4]) {
+            if constexpr (s == 1) Fmt<S>::load4(own_in + row * PWIN + dx, v);
+            else Fmt<float>::load4(own32 + row * PW + dx, v);
+        };
         float up[(D == 3) ? R : 1][4], dn[(D == 3) ? R : 1][4];
         (void)up;
         (void)dn;
         if constexpr (D == 3) {
 #pragma unroll
             for (int m = 0; m < R; ++m) {
-                Fmt<float>::load4(own - (m + 1) * PW, up[m]);
-                Fmt<float>::load4(own + (VY + m) * PW, dn[m]);
+                ld(-(m + 1), 0, up[m]);
+                ld(VY + m, 0, dn[m]);
             }
         }
         float res[VY][4];
 #pragma unroll
         for (int vy = 0; vy < VY; ++vy) {
             float L[4], Rr[4];
-            Fmt<float>::load4(own + vy * PW - 4, L);
-            Fmt<float>::load4(own + vy * PW + 4, Rr);
+            ld(vy, -4, L);
+            ld(vy, 4, Rr);
             const float(&ctr)[VY][4] = q[s - 1][js];
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
@@ -577,18 +591,6 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
             return;
         }
         if (tid == 0) consumed_hi = p;
-        const S *slot = inslot + J * SLOTIN;
-        if constexpr (!F32S) {
-            // convert the whole padded plane into level 0's FP32 ring
-            float *dst = ring32(0, J);
-            constexpr int C4 = PW / 4;
-            for (int t = tid; t < C4 * G::PH; t += NTHR) {
-                const int row = t / C4, col = t % C4;
-                float v4[4];
-                Fmt<S>::load4(slot + row * PWIN + 4 * col + (PADIN - 4), v4);
-                Fmt<float>::store4(dst + row * PW + 4 * col, v4);
-            }
-        }
         float v4[VY][4];
 #pragma unroll
         for (int vy = 0; vy < VY; ++vy) Fmt<S>::load4(inb + J * SLOTIN + vy * PWIN, v4[vy]);
@@ -607,10 +609,8 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                         for (int v = 0; v < 4; ++v) q[0][j][vy][v] = v4[vy][v];
             }
         }
-        if constexpr (F32S) {
-            // the input slot is level 0's ring: clamp its out-of-grid frame now (read from step k+1 on)
-            if (gh.ntask > 0) ghost_fill(reinterpret_cast<float *>(const_cast<S *>(slot)), gh, PW, ox, a.nx, tid, NTHR);
-        }
+        // the input slot is level 0's ring: clamp its out-of-grid frame now (read from step k+1 on)
+        if (gh_in.ntask > 0) ghost_fill<sizeof(S)>(inslot + J * SLOTIN, gh_in, PWIN, ox_in, a.nx, tid, NTHR);
     };
 
     // ---- one step
@@ -626,25 +626,24 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         if (tid == 0) {
             const int qn = k + G::PF;
             if (qn <= lmax) {
-                if (gh.ntask > 0) fence_proxy_async_smem();
+                if (gh_in.ntask > 0) fence_proxy_async_smem();
                 issue(qn);
             }
         }
-        // levels T..2 (and 1 when it reads a thread-written ring), highest first
-        constexpr int LOW = F32S ? 2 : 1;
-        SFor<0, T - LOW + 1>::run([&](auto ic) {
+        // levels T..2 highest first, then level 0 (the input), then level 1 (reads the input ring)
+        SFor<0, T - 1>::run([&](auto ic) {
             constexpr int s = T - decltype(ic)::value;
             level(IC<s>{}, Jc, CKc, k);
         });
         level0(Jc, CKc, k);
-        if constexpr (F32S) level(IC<1>{}, Jc, CKc, k);
+        level(IC<1>{}, Jc, CKc, k);
         // clamp frame of ring planes written in the previous step
         if (gh.ntask > 0) {
-            SFor<F32S ? 1 : 0, T>::run([&](auto sc) {
+            SFor<1, T>::run([&](auto sc) {
                 constexpr int s = decltype(sc)::value;
                 const int p = k - 1 - G::lag(s);
                 if (p >= lo[s] && p <= min(hi[s], last))
-                    ghost_fill(ring32(s, cmod(J - 1 - G::lag(s), QP)), gh, PW, ox, a.nx, tid, NTHR);
+                    ghost_fill<4>(ring32(s, cmod(J - 1 - G::lag(s), QP)), gh, PW, ox, a.nx, tid, NTHR);
             });
         }
         __syncthreads();
