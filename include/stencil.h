@@ -71,9 +71,14 @@ typedef enum {
  * consecutive x cells (a 512-cell row strip streamed along y); 3D 16 x 8
  * threads, each owning 4 x cells times rows_per_thread y rows (a 64-cell
  * wide tile streamed along z).  The strip/tile includes a halo of r*(t-1)
- * cells per side (x halo rounded up to 8) recomputed by neighbouring blocks
- * (overlapped blocking, Eq. 2), and each block streams `seg` rows/planes
- * plus r*t halo planes of the stream axis.
+ * cells per side (x halo rounded up to 16 bytes) recomputed by neighbouring
+ * blocks (overlapped blocking, Eq. 2).  2D: with the strips' y axes laid
+ * end to end, block b streams rows [b*seg, (b+1)*seg) of that sequence (one
+ * piece per strip it touches); the default `seg` gives every resident block
+ * slot of the device the same number of rows (once, or for kernels with a
+ * short loop body several times over).  3D: each tile's z axis is cut into
+ * slabs of `seg` planes, one block per (slab, tile), the tiles of a slab in
+ * consecutive blocks.  Every piece also streams r*t halo planes.
  */
 typedef struct {
     int kernel;          /* stencil_kernel */
@@ -81,7 +86,7 @@ typedef struct {
     int threads_x;       /* 0, or the compiled block width (2D 128, 3D 16) */
     int threads_y;       /* 0, or the compiled block height (3D 8) */
     int rows_per_thread; /* 3D: 2 or 4 */
-    int seg;             /* stream-axis extent per block, >= 1 */
+    int seg;             /* stream-axis rows/planes per block, >= 1 */
     int prefetch;        /* 0, or the compiled number of planes loaded ahead */
 } stencil_schedule;
 

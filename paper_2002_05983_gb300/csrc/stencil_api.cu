@@ -208,7 +208,7 @@ void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz,
 
 // Fill one pass of temporal degree t.  Pointers are set by the caller.
 int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, int t,
-              const stencil_schedule &s, const DevInfo &dev, Pass &ps)
+              const stencil_schedule &s, const DevInfo &dev, Pass &ps, bool batched = false)
 {
     const int D = h->dim, R = h->r;
     const int vy = D == 3 ? s.rows_per_thread : 1;
@@ -226,23 +226,43 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
     const int64_t nty = D == 3 ? (ny + e->cy - 1) / e->cy : 1;
     const int64_t ns = D == 3 ? nz : ny;
     const int64_t tiles = ntx * nty;
+    const int64_t slots = static_cast<int64_t>(dev.sms) * occ;
+    const int64_t minseg = std::max<int64_t>(64, 8 * t * (2 * R + 1));
+    // 2D: the strips laid end to end hold W rows, block b sweeps [b*seg, (b+1)*seg) of
+    // them.  3D: slabs of seg planes, the tiles of one slab in consecutive blocks (their
+    // boxes overlap by the halo; neighbours that run together share those reads in L2).
+    const bool flat = D == 2;
+    const int64_t W = tiles * ns;
     int64_t seg = s.seg;
     if (seg <= 0) {
-        // enough blocks for >= 4 waves (dynamic balance of edge tiles), but segments long
-        // against the pipeline fill of t*(2r+1) planes
-        const int64_t slots = static_cast<int64_t>(dev.sms) * occ;
-        const int64_t want = (4 * slots + tiles - 1) / tiles;
-        const int64_t minseg = std::max<int64_t>(64, 8 * t * (2 * R + 1));
-        seg = std::max<int64_t>((ns + want - 1) / want, minseg);
-        seg = std::min<int64_t>(seg, ns);
+        if (!flat) {
+            // >= 4 waves (dynamic balance of edge tiles), segments long against the fill
+            const int64_t want = (4 * slots + tiles - 1) / tiles;
+            seg = std::max<int64_t>((ns + want - 1) / want, minseg);
+        } else if (batched) {
+            // other grids fill the device: segments long against the pipeline fill
+            seg = std::max<int64_t>((W + 4 * slots - 1) / (4 * slots), minseg);
+        } else {
+            // Equal blocks, one per resident block slot: no SM waits on a partly filled
+            // last wave.  Kernels with a short unrolled body (queue period x levels x
+            // cells x FMA <= 400) run better as several equal waves of ~200-row blocks,
+            // which keeps blocks out of phase; long bodies lose instruction-cache hits
+            // when blocks on one SM run different phases (prologue/steady), so they
+            // keep one wave.
+            seg = (W + slots - 1) / slots;
+            const int64_t body = static_cast<int64_t>(2 * R + 1) * t * 4 * (4 * R + 1);
+            if (body <= 400) seg = std::min<int64_t>(seg, std::max<int64_t>(192, (W + 8 * slots - 1) / (8 * slots)));
+        }
     }
-    const int64_t nseg = (ns + seg - 1) / seg;
-    if (tiles * nseg > 0x7fffffffLL) return STENCIL_ERR_UNSUPPORTED;
+    seg = std::max<int64_t>(seg, 1);
+    seg = std::min<int64_t>(seg, flat ? W : ns);
+    const int64_t nblk = flat ? (W + seg - 1) / seg : tiles * ((ns + seg - 1) / seg);
+    if (nblk > 0x7fffffffLL || seg > 0x7fffffffLL) return STENCIL_ERR_UNSUPPORTED;
 
     ps.fn = e->fn;
     ps.t = t;
     ps.occ = occ;
-    ps.grid = dim3(static_cast<unsigned>(tiles * nseg));
+    ps.grid = dim3(static_cast<unsigned>(nblk));
     ps.block = dim3(e->tx, e->ty);
     ps.smem = e->smem;
     stn::SweepArgs &a = ps.a;
@@ -251,6 +271,7 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
     a.nz = static_cast<int>(nz);
     a.ns = static_cast<int>(ns);
     a.seg = static_cast<int>(seg);
+    a.flat = flat ? 1 : 0;
     a.ntx = static_cast<int>(ntx);
     a.nty = static_cast<int>(nty);
     a.timeout_ms = h->timeout_ms;
@@ -470,12 +491,12 @@ double analytic_ns(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, in
     const double bx = 4.0 * e->tx, by = D == 3 ? static_cast<double>(e->ty) * e->vy : 1.0;
     const double tiles = std::ceil(nx / static_cast<double>(e->cx)) * (D == 3 ? std::ceil(ny / static_cast<double>(e->cy)) : 1.0);
     const double ns_axis = D == 3 ? static_cast<double>(nz) : static_cast<double>(ny);
-    const double nseg = std::ceil(ns_axis / s.seg);
+    const double nblk = std::ceil(tiles * ns_axis / s.seg);
     // cell-level updates of one block: its thread region for every level over
-    // its segment plus the r*t stream halo; blocks run in waves of sms*occ
+    // its planes plus the r*t stream halo; blocks run in waves of sms*occ
     const double per_block = bx * by * t * (s.seg + static_cast<double>(t) * R) * (2.0 * D * R + 1.0);
     const double slots = 152.0 * std::max(occ, 1);
-    const double waves = std::ceil(tiles * nseg / slots);
+    const double waves = std::ceil(nblk / slots);
     const double warps = static_cast<double>(occ) * e->tx * e->ty / 32.0;
     const double eff = kFpEfficiency * std::min(1.0, warps / kFullWarps);
     const double t_fp = waves * per_block * std::max(occ, 1) / (kFp32InstrRate / 152.0 * std::max(eff, 0.02));
@@ -609,7 +630,7 @@ int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cuda
         x.t = t;
         x.L = b.iters / t;
         x.rows = h->dim == 3 ? s.rows_per_thread : 1;
-        int rc = plan_pass(h, b.nx, b.ny, b.nz, b.dtype, t, s, dev, x.ps);
+        int rc = plan_pass(h, b.nx, b.ny, b.nz, b.dtype, t, s, dev, x.ps, true);
         if (rc) return rc;
         x.e = registry().find(h->dim, h->r, t, x.rows, b.dtype, s.threads_x, s.threads_y);
         if (!x.e) return STENCIL_ERR_UNSUPPORTED;

@@ -21,7 +21,7 @@ template <int D, int R, int T, int VY, int ES, int TX, int TY> struct Geo {
     static constexpr int PADIN = 16 / ES;              // input row padding (elements)
     static constexpr int BX = 4 * TX;                  // thread-region width (cells)
     static constexpr int BY = (D == 3) ? TY * VY : 1;  // thread-region rows (3D)
-    static constexpr int HTX = rup((T - 1) * R, 8);    // x halo of levels 1..T (multiple of 8)
+    static constexpr int HTX = rup((T - 1) * R, PADIN);   // x halo of levels 1..T (16-byte multiple)
     static constexpr int HTY = (D == 3) ? (T - 1) * R : 0;
     static constexpr int CX = BX - 2 * HTX;            // compute tile (Eq. 2: bsize - 2 t r)
     static constexpr int CY = (D == 3) ? BY - 2 * HTY : 1;

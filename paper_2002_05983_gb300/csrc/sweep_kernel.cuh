@@ -54,7 +54,8 @@ struct SweepArgs {
     unsigned *status;     // sticky device status word
     int nx, ny, nz;       // grid extents (2D: nz = 1)
     int ns;               // extent of the streaming axis (2D: ny, 3D: nz)
-    int seg;              // streaming-axis extent per block
+    int seg;              // stream-axis rows/planes per block
+    int flat;             // 1: blocks split the tile columns laid end to end; 0: slabs of seg planes
     int ntx, nty;         // tile counts in x and y (nty = 1 in 2D)
     int timeout_ms;       // limit of every bounded wait
     int fault_plane;      // test hook: never load this input plane (< 0: off)
@@ -300,12 +301,12 @@ __device__ __forceinline__ void mbar_inval(uint32_t bar)
 }
 
 // ------------------------------------------------------------------ one tile
-// One x (and y) tile and stream segment of one pass, by one thread block.
-// `tile` indexes tile_x + ntx * (tile_y + nty * segment).  Returns false if a
-// bounded wait expired (the device status word is then set).  Leaves the
-// block's shared memory free for the next tile.
+// Planes [Z0, Z1) of tile column `col` = tile_x + ntx * tile_y of one pass, by
+// one thread block.  Returns false if a bounded wait expired (the device
+// status word is then set).  Leaves the block's shared memory free for the
+// next piece.
 template <int D, int R, int T, int VY, typename S, int TX, int TY>
-__device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepArgs &a, int tile,
+__device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepArgs &a, int col, int Z0, int Z1,
                                            unsigned char *smem)
 {
     using G = Geo<D, R, T, VY, static_cast<int>(sizeof(S)), TX, TY>;
@@ -332,22 +333,14 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
 
-    // ---- tile and segment of this block
-    int b = tile;
-    const int tile_x = b % a.ntx;
-    b /= a.ntx;
-    int tile_y = 0;
-    if (D == 3) {
-        tile_y = b % a.nty;
-        b /= a.nty;
-    }
+    // ---- tile of this piece
+    const int tile_x = col % a.ntx;
+    const int tile_y = (D == 3) ? col / a.ntx : 0;
     const int gx0 = tile_x * G::CX - G::HTX;          // thread-region origin
     const int gy0 = (D == 3) ? tile_y * G::CY - G::HTY : 0;
     const int ox = gx0 - 4;                            // padded FP32 plane origin
     const int oy = (D == 3) ? gy0 - R : 0;
     const int ox_in = gx0 - PADIN;                     // padded input plane origin
-    const int Z0 = b * a.seg;
-    const int Z1 = min(Z0 + a.seg, a.ns);
     const int last = a.ns - 1;
 
     // ---- this thread's cells
@@ -683,14 +676,42 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     return !aborted;
 }
 
+// Work of block b.  flat: planes [b*seg, (b+1)*seg) of the tile columns laid
+// end to end (column c holds planes c*ns .. c*ns + ns - 1), a range that
+// crosses the end of a column being swept as one piece per column.  Slabs:
+// column b mod (ntx*nty), planes [j*seg, (j+1)*seg) with j = b / (ntx*nty),
+// so blocks running together cover neighbouring tiles of the same planes and
+// share their overlapping halo reads in L2.
+template <int D, int R, int T, int VY, typename S, int TX, int TY>
+__device__ __forceinline__ bool sweep_block(const CUtensorMap *tmap, const SweepArgs &a, int b, unsigned char *smem)
+{
+    const int cols = a.ntx * a.nty;
+    if (!a.flat) {
+        const int z0 = (b / cols) * a.seg;
+        return sweep_tile<D, R, T, VY, S, TX, TY>(tmap, a, b % cols, z0, min(z0 + a.seg, a.ns), smem);
+    }
+    const int64_t W = static_cast<int64_t>(cols) * a.ns;
+    int64_t w = static_cast<int64_t>(b) * a.seg;
+    const int64_t we = min(w + a.seg, W);
+    bool ok = true;
+    while (ok && w < we) {
+        const int col = static_cast<int>(w / a.ns);
+        const int z0 = static_cast<int>(w - static_cast<int64_t>(col) * a.ns);
+        const int z1 = static_cast<int>(min(static_cast<int64_t>(a.ns), z0 + (we - w)));
+        ok = sweep_tile<D, R, T, VY, S, TX, TY>(tmap, a, col, z0, z1, smem);
+        w += z1 - z0;
+    }
+    return ok;
+}
+
 // ------------------------------------------------------------------ kernels
-// One pass over the grid: block b sweeps tile b.
+// One pass over the grid: block b sweeps its planes of the tile columns (sweep_block).
 template <int D, int R, int T, int VY, typename S, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY)
     sweep_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ SweepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    sweep_tile<D, R, T, VY, S, TX, TY>(&tmap, a, static_cast<int>(blockIdx.x), smem);
+    sweep_block<D, R, T, VY, S, TX, TY>(&tmap, a, static_cast<int>(blockIdx.x), smem);
 }
 
 // Persistent sweep of many grids of one kernel class, all passes, from a device tile
@@ -774,7 +795,7 @@ __global__ void __launch_bounds__(TX *TY)
         __syncthreads();
         if (!s_ok) break;
         const SweepArgs a = B.args[task];
-        const bool done = sweep_tile<D, R, T, VY, S, TX, TY>(D == 3 ? B.maps + task : nullptr, a, q - tk.first, smem);
+        const bool done = sweep_block<D, R, T, VY, S, TX, TY>(D == 3 ? B.maps + task : nullptr, a, q - tk.first, smem);
         __syncthreads();
         if (tid == 0 && task != B.fault_task) {
             __threadfence();

@@ -85,7 +85,7 @@ def test_schedules_bit_identical_to_naive(dim, r):
     scheds = []
     for vy in ((1,) if dim == 2 else (2, 4)):
         for t in range(1, st.stencil_max_t(dim, r, 0, vy) + 1):
-            for seg in (0, 7, 61):
+            for seg in (0, 1, 7, 61, 5000):   # 5000: one block sweeps several strips/tiles
                 scheds.append(dict(kernel=st.KERNEL_STREAM, t=t, seg=seg, rows_per_thread=vy))
     for sc in scheds:
         try:
