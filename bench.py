@@ -119,13 +119,22 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def kernel_source_hash(csrc):
+    """sha256[:16] of the streaming kernel's sources (kernel body, then tile geometry)."""
+    h = hashlib.sha256()
+    for name in ("sweep_kernel.cuh", "sweep_cfg.h"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_for(dim, r, t, dtype="f32"):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-    src = os.path.join(ROOT, "paper_2002_05983_gb300", "csrc", "sweep_kernel.cuh")
+    csrc = os.path.join(ROOT, "paper_2002_05983_gb300", "csrc")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = kernel_source_hash(csrc)
     for ln in open(path):
         f = ln.split()
         if len(f) == 6 and not ln.startswith("#") and f[0] == h and f[1:5] == [str(dim), str(r), str(t), dtype]:
