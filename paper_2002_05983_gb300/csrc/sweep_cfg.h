@@ -9,6 +9,11 @@ constexpr int kMaxK = 25;            // 2*3*4 + 1 coefficients
 constexpr int kSmemHeader = 1024;    // mbarriers + abort flag
 constexpr int kMaxDepthIn = 64;
 constexpr unsigned kStatusTimeout = 1u;
+// Unrolled-chunk sizes in FMA per thread (steps x levels x cells x (2*D*r+1)):
+// 3D kernels whose rotating chunk exceeds kRotMaxFma use shifting chunks of about
+// kChunkFma (see Geo::U).
+constexpr int kRotMaxFma = 600;
+constexpr int kChunkFma = 300;
 
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr int rup(int a, int b) { return cdiv(a, b) * b; }
@@ -31,9 +36,20 @@ template <int D, int R, int T, int VY, int ES, int TX, int TY> struct Geo {
     static constexpr int SLOT32 = rup(PW * PH, 32);    // floats per FP32 ring slot
     static constexpr int SLOTIN = rup(PWIN * PH * ES, 128) / ES;   // elements per input slot
     static constexpr int PFMIN = (D == 2) ? 4 : 2;
+    // Steps per unrolled chunk.  The register queue of a level holds 2r+1 planes;
+    // with U = QP steps per chunk it rotates through fixed registers (ROT).  In
+    // 3D, a rotating chunk larger than kRotMaxFma misses the instruction cache, so
+    // chunks of U < QP steps append to a queue of QP + U registers and shift it
+    // down by U planes at the chunk's end (QP moves per cell and level every U
+    // steps): measured 1.2-1.4x faster for 3D r = 3, 4.  2D keeps the rotating
+    // queue at every size: there the moves cost more than the misses they avoid.
+    static constexpr int BODY = T * VY * 4 * (2 * D * R + 1);
+    static constexpr bool ROT = D == 2 || QP * BODY <= kRotMaxFma;
+    static constexpr int U = ROT ? QP : (kChunkFma / BODY >= 1 ? kChunkFma / BODY : 1);
+    static constexpr int NQ = ROT ? QP : QP + U;       // queue registers per level and cell
     static constexpr int LAG1 = R;                     // steps level 1 trails the input
     static constexpr int KEEP = R + 1;                 // input slots held besides prefetch
-    static constexpr int DEPTH = QP * cdiv(KEEP + PFMIN, QP);   // input ring slots
+    static constexpr int DEPTH = U * cdiv(KEEP + PFMIN, U);     // input ring slots (chunk multiple)
     static constexpr int PF = DEPTH - KEEP;            // planes loaded ahead of use
     static constexpr int NRING = T - 1;                // FP32 rings written by levels 1..T-1
     static constexpr size_t SMEM = static_cast<size_t>(kSmemHeader) +

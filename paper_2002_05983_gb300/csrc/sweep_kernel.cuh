@@ -315,6 +315,8 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     static_assert(D == 3 || (VY == 1 && TY == 1), "2D keeps one row per thread");
     static_assert(G::OK, "tile too small for this temporal degree");
     constexpr int QP = G::QP;
+    constexpr int U = G::U, NQ = G::NQ;
+    constexpr bool ROT = G::ROT;
     constexpr bool F32S = G::F32S;
     constexpr int PADIN = G::PADIN;
     constexpr int K2 = 2 * D;
@@ -450,11 +452,11 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         for (int q = k0; q <= qe; ++q) issue(q);
     }
 
-    float q[T][QP][VY][4];
+    float q[T][NQ][VY][4];
 #pragma unroll
     for (int s = 0; s < T; ++s)
 #pragma unroll
-        for (int j = 0; j < QP; ++j)
+        for (int j = 0; j < NQ; ++j)
 #pragma unroll
             for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
@@ -463,21 +465,44 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     int consumed_hi = k0 - 1;   // last input plane waited for by thread 0
     bool aborted = false;
 
-    // per-chunk state (a chunk is QP steps; kb is a multiple of QP)
-    int kb = k0 - k0 % QP;
+    // per-chunk state (a chunk is U steps; kb is a multiple of U)
+    int kb = k0 - k0 % U;
     int kb_mod = kb % DEPTH;
     int lap = kb / DEPTH;
     uint32_t bar0 = 0, par = 0;
     const S *inb = nullptr;     // own cell 0 in the input slot of plane kb
-    const S *inbp = nullptr;    // own cell 0 in the input slot of plane kb - QP
+    const S *inbp = nullptr;    // ROT: own cell 0 in the input slot of plane kb - QP
     S *inslot = nullptr;        // input slot of plane kb
+    // shifting queue: FP32 ring slot of plane kb - lag(s) for level s = 1..T
+    int rb[T + 1];
+#pragma unroll
+    for (int s = 1; s <= T; ++s) rb[s] = cmod(kb - G::lag(s), QP);
+
+    // queue index of the plane level s computes at chunk step J
+    auto qnew = [](int s, int J) constexpr { return ROT ? cmod(J - G::lag(s), QP) : QP + J; };
+    // queue index of level s-1's plane p+e, read by level s at chunk step J (|e| <= R);
+    // level s-1 has computed plane p+R in this step (s = 1) or in the previous one (s >= 2)
+    auto qrd = [](int s, int J, int e) constexpr {
+        return ROT ? cmod(J - G::lag(s) + e, QP) : (s == 1 ? QP + J : QP + J - 1) - (R - e);
+    };
+    // FP32 ring slot of level s's plane k - off - lag(s) at chunk step J (off = 0 or 1)
+    auto rslot = [&](int s, int J, int off) -> int {
+        if constexpr (ROT) {
+            return cmod(J - off - G::lag(s), QP);
+        } else {
+            int j = rb[s] + J - off;
+            j = j >= QP ? j - QP : j;
+            return j < 0 ? j + QP : j;
+        }
+    };
 
     // ---- one time level s of step k
     auto level = [&](auto sc, auto Jc, auto CKc, int k) {
         constexpr int s = decltype(sc)::value;
         constexpr int J = decltype(Jc)::value;
         constexpr bool CK = decltype(CKc)::value;
-        constexpr int js = cmod(J - G::lag(s), QP);    // queue/ring slot of plane p
+        constexpr int jn = qnew(s, J);                 // own queue index of plane p
+        constexpr int jc = qrd(s, J, 0);               // level s-1's queue index of plane p
         const int p = k - G::lag(s);
         if constexpr (CK) {
             if (p < lo[s] || p > hi[s]) return;
@@ -486,7 +511,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
 #pragma unroll
                     for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
-                        for (int v = 0; v < 4; ++v) q[s][js][vy][v] = q[s][cmod(js - 1, QP)][vy][v];
+                        for (int v = 0; v < 4; ++v) q[s][jn][vy][v] = q[s][ROT ? cmod(jn - 1, QP) : jn - 1][vy][v];
                 }
                 return;
             }
@@ -496,10 +521,16 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         const S *own_in = nullptr;
         const float *own32 = nullptr;
         if constexpr (s == 1) {
-            constexpr int d = J - R;    // input slot of plane k-R relative to plane kb
-            own_in = d >= 0 ? inb + d * SLOTIN : inbp + (d + QP) * SLOTIN;
+            if constexpr (ROT) {
+                constexpr int d = J - R;    // input slot of plane k-R relative to plane kb
+                own_in = d >= 0 ? inb + d * SLOTIN : inbp + (d + QP) * SLOTIN;
+            } else {
+                int d = kb_mod + J - R;     // input slot of plane k-R
+                d = d < 0 ? d + DEPTH : d;
+                own_in = ring_in + d * SLOTIN + toffin;
+            }
         } else {
-            own32 = ring32(s - 1, js) + toff;
+            own32 = ring32(s - 1, rslot(s, J, 0)) + toff;
         }
         auto ld = [&](int row, int dx, float (&v)[4]) {
             if constexpr (s == 1) Fmt<S>::load4(own_in + row * PWIN + dx, v);
@@ -521,7 +552,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
             float L[4], Rr[4];
             ld(vy, -4, L);
             ld(vy, 4, Rr);
-            const float(&ctr)[VY][4] = q[s - 1][js];
+            const float(&ctr)[VY][4] = q[s - 1][jc];
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 float acc = __fmul_rn(cf[0], ctr[vy][v]);
@@ -540,8 +571,8 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                         acc = __fmaf_rn(cf[cb + 2], sv, acc);
                         acc = __fmaf_rn(cf[cb + 3], nv, acc);
                     }
-                    acc = __fmaf_rn(cf[cb + K2 - 2], q[s - 1][cmod(js - i, QP)][vy][v], acc);
-                    acc = __fmaf_rn(cf[cb + K2 - 1], q[s - 1][cmod(js + i, QP)][vy][v], acc);
+                    acc = __fmaf_rn(cf[cb + K2 - 2], q[s - 1][qrd(s, J, -i)][vy][v], acc);
+                    acc = __fmaf_rn(cf[cb + K2 - 1], q[s - 1][qrd(s, J, i)][vy][v], acc);
                 }
                 res[vy][v] = acc;
             }
@@ -555,17 +586,17 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                     if (ystore[vy]) Fmt<S>::store4(o + vy * a.nx, res[vy]);
             }
         } else {
-            float *dst = ring32(s, js) + toff;
+            float *dst = ring32(s, rslot(s, J, 0)) + toff;
 #pragma unroll
             for (int vy = 0; vy < VY; ++vy) {
                 Fmt<float>::store4(dst + vy * PW, res[vy]);
 #pragma unroll
-                for (int v = 0; v < 4; ++v) q[s][js][vy][v] = res[vy][v];
+                for (int v = 0; v < 4; ++v) q[s][jn][vy][v] = res[vy][v];
             }
             if constexpr (CK) {
                 if (p == 0) {   // top clamp: planes -r..-1 of this level equal plane 0
 #pragma unroll
-                    for (int j = 0; j < QP; ++j)
+                    for (int j = 0; j < NQ; ++j)
 #pragma unroll
                         for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
@@ -586,7 +617,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
 #pragma unroll
                 for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) q[0][J][vy][v] = q[0][cmod(J - 1, QP)][vy][v];
+                    for (int v = 0; v < 4; ++v) q[0][qnew(0, J)][vy][v] = q[0][ROT ? cmod(J - 1, QP) : QP + J - 1][vy][v];
                 return;
             }
         }
@@ -603,11 +634,11 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
 #pragma unroll
         for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) q[0][J][vy][v] = v4[vy][v];
+            for (int v = 0; v < 4; ++v) q[0][qnew(0, J)][vy][v] = v4[vy][v];
         if constexpr (CK) {
             if (p == 0) {
 #pragma unroll
-                for (int j = 0; j < QP; ++j)
+                for (int j = 0; j < NQ; ++j)
 #pragma unroll
                     for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
@@ -648,25 +679,38 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                 constexpr int s = decltype(sc)::value;
                 const int p = k - 1 - G::lag(s);
                 if (p >= lo[s] && p <= min(hi[s], last))
-                    ghost_fill<4>(ring32(s, cmod(J - 1 - G::lag(s), QP)), gh, PW, ox, a.nx, tid, NTHR);
+                    ghost_fill<4>(ring32(s, rslot(s, J, 1)), gh, PW, ox, a.nx, tid, NTHR);
             });
         }
         __syncthreads();
         aborted = (*sflag != 0);
     };
 
-    for (; kb <= k1 && !aborted; kb += QP) {
+    for (; kb <= k1 && !aborted; kb += U) {
         par = static_cast<uint32_t>((lap - lap0) & 1);
         bar0 = smem_addr(bars + kb_mod);
         inslot = ring_in + kb_mod * SLOTIN;
         inb = inslot + toffin;
-        inbp = ring_in + (kb_mod == 0 ? DEPTH - QP : kb_mod - QP) * SLOTIN + toffin;
-        if (kb >= kA && kb + QP - 1 <= kB) {
-            SFor<0, QP>::run([&](auto Jc) { step(Jc, std::false_type{}); });
+        if constexpr (ROT) inbp = ring_in + (kb_mod == 0 ? DEPTH - QP : kb_mod - QP) * SLOTIN + toffin;
+        if (kb >= kA && kb + U - 1 <= kB) {
+            SFor<0, U>::run([&](auto Jc) { step(Jc, std::false_type{}); });
         } else {
-            SFor<0, QP>::run([&](auto Jc) { step(Jc, std::true_type{}); });
+            SFor<0, U>::run([&](auto Jc) { step(Jc, std::true_type{}); });
         }
-        kb_mod += QP;
+        if constexpr (!ROT) {
+            // shift every queue down by the U planes appended in this chunk
+#pragma unroll
+            for (int s = 0; s < T; ++s)
+#pragma unroll
+                for (int j = 0; j < QP; ++j)
+#pragma unroll
+                    for (int vy = 0; vy < VY; ++vy)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) q[s][j][vy][v] = q[s][j + U][vy][v];
+#pragma unroll
+            for (int s = 1; s <= T; ++s) rb[s] = rb[s] + U >= QP ? rb[s] + U - QP : rb[s] + U;
+        }
+        kb_mod += U;
         if (kb_mod == DEPTH) {
             kb_mod = 0;
             ++lap;
@@ -698,15 +742,18 @@ template <int D, int R, int T, int VY, typename S, int TX, int TY>
 __device__ __forceinline__ bool sweep_block(const CUtensorMap *tmap, const SweepArgs &a, int b, unsigned char *smem)
 {
     const int cols = a.ntx * a.nty;
-    if (!a.flat) {
+    int64_t w, we;
+    if (a.flat) {
+        w = static_cast<int64_t>(b) * a.seg;
+        we = min(w + a.seg, static_cast<int64_t>(cols) * a.ns);
+    } else {   // slab j = b / cols of column b mod cols
+        const int col = b % cols;
         const int z0 = (b / cols) * a.seg;
-        return sweep_tile<D, R, T, VY, S, TX, TY>(tmap, a, b % cols, z0, min(z0 + a.seg, a.ns), smem);
+        w = static_cast<int64_t>(col) * a.ns + z0;
+        we = static_cast<int64_t>(col) * a.ns + min(z0 + a.seg, a.ns);
     }
-    const int64_t W = static_cast<int64_t>(cols) * a.ns;
-    int64_t w = static_cast<int64_t>(b) * a.seg;
-    const int64_t we = min(w + a.seg, W);
     bool ok = true;
-    while (ok && w < we) {
+    while (ok && w < we) {   // one sweep_tile call site: the kernel body is instantiated once
         const int col = static_cast<int>(w / a.ns);
         const int z0 = static_cast<int>(w - static_cast<int64_t>(col) * a.ns);
         const int z1 = static_cast<int>(min(static_cast<int64_t>(a.ns), z0 + (we - w)));
