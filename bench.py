@@ -115,8 +115,39 @@ class Clocks:
                     reasons.add(n)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+               "samples": len(sm)}
+        watts = []
+        for ln in getattr(self, "lines", []):
+            try:
+                watts.append(float(ln.split(",")[2]))
+            except (IndexError, ValueError):
+                pass
+        if watts:
+            out["power_w"] = round(statistics.median(watts), 1)
+        return out
+
+
+# ---- replicas (one process per GPU, weak scaling): rank environment and timing reduction
+def rank_env():
+    """(world, rank, local rank) from the torchrun environment (1, 0, 0 without it)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def reduce_max(value: float, dist=None, device="cpu") -> float:
+    """Largest `value` over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank processed units_per_rank in at most `seconds`."""
+    return units_per_rank * world / seconds
 
 
 def kernel_source_hash(csrc):
@@ -167,8 +198,8 @@ def oracle_leg(steps: int, warmup: int):
 
 
 def reference_main(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    _, rank, _ = rank_env()
+    if rank != 0:   # the oracle arm runs once, on rank 0; other ranks exit without work
         return 0
     g, dt, cores, sample = oracle_leg(args.steps, args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": round(g, 4), "unit": "GCell/s",
@@ -411,9 +442,7 @@ def main():
     import paper_2002_05983_gb300 as st
     from paper_2002_05983_gb300 import metrics
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -464,16 +493,13 @@ def main():
     elapsed = e_start.elapsed_time(e_stop) / 1e3
     if st.stencil_get_device_status() != 0:
         raise RuntimeError("device status reports a timed-out kernel")
-    if dist:
-        tt = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = reduce_max(elapsed, dist, "cuda")
 
     per_r = {}
     for r in RADII:
         per_r[r] = sum(evs[k][r][0].elapsed_time(evs[k][r][1]) for k in range(args.steps)) / 1e3 / args.steps
     cells_step = NX * NY * ITERS * len(RADII)
-    value = cells_step * args.steps * world / elapsed / 1e9
+    value = job_rate(cells_step * args.steps, world, elapsed) / 1e9
     flops_step = sum(NX * NY * ITERS * metrics.flop_per_cell(2, r) for r in RADII)
 
     # ---- end to end through the C ABI on pinned host buffers (copies inside the timed region)
@@ -487,10 +513,7 @@ def main():
             stencils[r].run_host(host, host_out, ITERS)
     barrier()
     e2e_el = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([e2e_el], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_el = float(tt.item())
+    e2e_el = reduce_max(e2e_el, dist, "cuda")
     for name, (dst, src) in (("h2d", (x, host)), ("d2h", (host_out, out))):
         c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c0.record()
@@ -499,7 +522,7 @@ def main():
         c1.synchronize()
         log(f"rank {rank}: {name} copy of {src.numel() * 4 / 2**30:.0f} GiB pinned: "
             f"{src.numel() * 4 / c0.elapsed_time(c1) / 1e6:.1f} GB/s")
-    e2e = {"value": round(cells_step * e2e_steps * world / e2e_el / 1e9, 3), "unit": "GCell/s",
+    e2e = {"value": round(job_rate(cells_step * e2e_steps, world, e2e_el) / 1e9, 3), "unit": "GCell/s",
            "h2d_bytes_per_step": host.numel() * 4 * len(RADII),
            "d2h_bytes_per_step": host_out.numel() * 4 * len(RADII)}
 
@@ -549,6 +572,9 @@ def main():
     clk = clk.summary()
     if clk:
         line["clocks"] = clk
+        if clk.get("power_w"):
+            line["power"] = {"board_w_median": clk["power_w"],
+                             "gflops_per_w": round(line["gflops"] / world / clk["power_w"], 2)}
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         g, dt, cores, sample = oracle_leg(1, 0)
         line["cpu_baseline"] = {"value": round(g, 4), "unit": "GCell/s", "cores": cores, "kind": "oracle",

@@ -1,0 +1,73 @@
+"""Multi-rank host logic of bench.py on CPU: two gloo ranks (world size 2).
+
+Replicas sweep independent grids, so the only cross-rank step is the timing
+reduction: the job's time is the slowest rank's, and the job's throughput is
+the units of all ranks over that time.  The reference (oracle) arm runs on
+rank 0 only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w, r, lr = bench.rank_env()
+        elapsed = [0.75, 1.25][rank]            # rank 1 is the slower one
+        slow = bench.reduce_max(elapsed, dist, "cpu")
+        units = 1000.0 * (rank + 1)             # rank-local count, only rank 0's is used below
+        dist.barrier()
+        q.put((r, w, lr, slow, bench.job_rate(units, w, slow)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_to_the_slowest_rank():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [g[0] for g in got] == [0, 1]
+    assert all(g[1] == 2 and g[2] == g[0] for g in got)
+    assert all(g[3] == 1.25 for g in got)                 # max over ranks, on every rank
+    assert got[0][4] == pytest.approx(1000.0 * 2 / 1.25)  # units x world / slowest time
+
+
+def test_single_process_defaults():
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    out = subprocess.run([sys.executable, "-c", "import bench; print(bench.rank_env())"], cwd=ROOT, env=env,
+                         capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.strip() == "(1, 0, 0)"
+    assert bench.reduce_max(2.5) == 2.5
+    assert bench.job_rate(10.0, 1, 2.0) == 5.0
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, WORLD_SIZE="2", RANK="1", LOCAL_RANK="1")
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2"], cwd=ROOT, env=env,
+                         capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0
+    assert out.stdout.strip() == ""
