@@ -290,7 +290,8 @@ def suite_main(args):
         x = _rand(shape, f32, 0)
         out = torch.empty_like(x)
         n = x.numel()
-        for r in RADII:
+        radii = [int(v) for v in args.radii.split(",")]
+        for r in radii:
             s = st.Stencil(dim, r, gen.coefficients(dim, r))
             for vy in ((1,) if dim == 2 else (2, 4)):
                 for t in range(1, st.stencil_max_t(dim, r, 0, vy) + 1):
@@ -307,7 +308,7 @@ def suite_main(args):
         # parity on the seeded crop at the full step count (clamp at the crop's own edges)
         side = 1024 if dim == 2 else 128
         f = crop_input(side) if dim == 2 else gen.workload_grid(3, side, side, side)
-        for r in RADII:
+        for r in radii:
             c = gen.coefficients(dim, r)
             s = st.Stencil(dim, r, c)
             got = s.run(torch.from_numpy(f).cuda(), iters).cpu().numpy()
@@ -408,6 +409,11 @@ def tune_main(args):
            "regret_model_test": stats(res["test"], "regret_model"),
            "regret_analytic_test": stats(res["test"], "regret_analytic"),
            "regret_model_train": stats(res["train"], "regret_model"),
+           "analytic_model_accuracy": {
+               "measured_over_predicted_median": round(float(np.median(res["analytic_ratio"])), 3),
+               "p10": round(float(np.percentile(res["analytic_ratio"], 10)), 3),
+               "p90": round(float(np.percentile(res["analytic_ratio"], 90)), 3),
+               "rows": int(len(res["analytic_ratio"]))},
            "test_problems": [dict(r["problem"], best_ns=round(r["best_ns"], 5),
                                   regret_model=round(r["regret_model"], 4),
                                   regret_analytic=round(r["regret_analytic"], 4)) for r in res["test"]]}
@@ -424,6 +430,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--suite", choices=["sweep2d", "sweep3d", "precision", "batch"], default=None,
                     help="other workloads: t sweeps, 16-bit storage, 96-grid batch (JSON lines)")
+    ap.add_argument("--radii", default="1,2,3,4",
+                    help="radii of the sweep2d/sweep3d suites (1..6; the paper's range is 1..4)")
     ap.add_argument("--tune-eval", action="store_true",
                     help="measure all schedules of seeded problems, train the cost model, report regret")
     ap.add_argument("--case", default=None,

@@ -3,7 +3,7 @@
  *
  * The operation (Zohouri, Podobas, Matsuoka, "High-Performance High-Order
  * Stencil Computation on FPGAs Using OpenCL", Section IV.A, Eq. 1): `iters`
- * Jacobi steps of a 2D or 3D star stencil of radius r = 1..4,
+ * Jacobi steps of a 2D or 3D star stencil of radius r = 1..6,
  *
  *   g(p) = c[0] f(p) + sum_{i=1..r} sum_{d} c[1 + (i-1)*2*dim + d] f(clamp(p + i*e_d)),
  *
@@ -72,13 +72,15 @@ typedef enum {
  * threads, each owning 4 x cells times rows_per_thread y rows (a 64-cell
  * wide tile streamed along z).  The strip/tile includes a halo of r*(t-1)
  * cells per side (x halo rounded up to 16 bytes) recomputed by neighbouring
- * blocks (overlapped blocking, Eq. 2).  2D: with the strips' y axes laid
- * end to end, block b streams rows [b*seg, (b+1)*seg) of that sequence (one
- * piece per strip it touches); the default `seg` gives every resident block
- * slot of the device the same number of rows (once, or for kernels with a
- * short loop body several times over).  3D: each tile's z axis is cut into
- * slabs of `seg` planes, one block per (slab, tile), the tiles of a slab in
- * consecutive blocks.  Every piece also streams r*t halo planes.
+ * blocks (overlapped blocking, Eq. 2).  Block order: the stream axis is cut
+ * into slabs of `seg` rows/planes, one block per (slab, strip/tile), the
+ * strips/tiles of a slab in consecutive blocks; except for 2D kernels with a
+ * long unrolled body ((2r+1)*t*4*(4r+1) > 400 FMA, e.g. r >= 2 at t >= 2) or
+ * t >= 5, where the strips' y axes are laid end to end and block b streams
+ * rows [b*seg, (b+1)*seg) of that sequence (one piece per strip it touches);
+ * there the default `seg` gives every resident block slot of the device the
+ * same number of rows (once for long bodies, else in ~200-row blocks).  Every
+ * piece also streams r*t halo planes.
  */
 typedef struct {
     int kernel;          /* stencil_kernel */
@@ -110,7 +112,7 @@ typedef enum {
     STENCIL_TUNE_MODEL = 2       /* pick the minimum predicted by a trained cost model */
 } stencil_tune_mode;
 
-/* Create a stencil of dimension `dim` (2 or 3) and radius 1..4 with
+/* Create a stencil of dimension `dim` (2 or 3) and radius 1..6 with
  * K = 2*dim*radius + 1 FP32 coefficients read from host memory `coeffs`
  * (layout above; copied, the caller keeps ownership).  Allocates no device
  * memory.  Errors: INVALID_ARG. */

@@ -76,6 +76,8 @@ const void *naive_fn(int dim, int r, int dtype)
         case 2: return pick<2, 2>(dtype);
         case 3: return pick<2, 3>(dtype);
         case 4: return pick<2, 4>(dtype);
+        case 5: return pick<2, 5>(dtype);
+        case 6: return pick<2, 6>(dtype);
         }
     } else if (dim == 3) {
         switch (r) {
@@ -83,6 +85,8 @@ const void *naive_fn(int dim, int r, int dtype)
         case 2: return pick<3, 2>(dtype);
         case 3: return pick<3, 3>(dtype);
         case 4: return pick<3, 4>(dtype);
+        case 5: return pick<3, 5>(dtype);
+        case 6: return pick<3, 6>(dtype);
         }
     }
     return nullptr;

@@ -5,11 +5,13 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "sweep_cfg.h"
+
 namespace stn {
 
 struct NaiveArgs {
     int nx, ny, nz;
-    float c[25];
+    float c[kMaxK];
 };
 
 // __global__ naive_kernel<dim, r, S>(const S* in, S* out, NaiveArgs) for dtype 0/1/2, or nullptr.

@@ -11,6 +11,7 @@ struct KernelEntry {
     int tx, ty;                 // block shape
     int cx, cy, htx, hty;       // compute tile and thread-region halo
     int pf;                     // planes loaded ahead of use
+    int padin;                  // input-plane x padding per side (cells): TMA box width 4*tx + 2*padin
     size_t smem;                // dynamic shared memory bytes
     const void *fn;             // __global__ sweep_kernel<dim, r, t, vy, S, tx, ty>
     const void *pfn;            // __global__ sweep_persistent<dim, r, t, vy, S, tx, ty>
@@ -40,6 +41,18 @@ int list_3d_f16_r1(const KernelEntry **e);
 int list_3d_f16_r2(const KernelEntry **e);
 int list_3d_f16_r3(const KernelEntry **e);
 int list_3d_f16_r4(const KernelEntry **e);
+int list_2d_f32_r5(const KernelEntry **e);
+int list_2d_f32_r6(const KernelEntry **e);
+int list_3d_f32_r5(const KernelEntry **e);
+int list_3d_f32_r6(const KernelEntry **e);
+int list_2d_bf16_r5(const KernelEntry **e);
+int list_2d_bf16_r6(const KernelEntry **e);
+int list_3d_bf16_r5(const KernelEntry **e);
+int list_3d_bf16_r6(const KernelEntry **e);
+int list_2d_f16_r5(const KernelEntry **e);
+int list_2d_f16_r6(const KernelEntry **e);
+int list_3d_f16_r5(const KernelEntry **e);
+int list_3d_f16_r6(const KernelEntry **e);
 
 }  // namespace stn
 
@@ -47,6 +60,7 @@ int list_3d_f16_r4(const KernelEntry **e);
 #define STN_E(D, R, T, VY, S, DT, TX, TY)                                                          \
     {D, R, T, VY, DT, TX, TY, STN_G(D, R, T, VY, S, TX, TY)::CX, STN_G(D, R, T, VY, S, TX, TY)::CY, \
      STN_G(D, R, T, VY, S, TX, TY)::HTX, STN_G(D, R, T, VY, S, TX, TY)::HTY,                        \
-     STN_G(D, R, T, VY, S, TX, TY)::PF, STN_G(D, R, T, VY, S, TX, TY)::SMEM,                        \
+     STN_G(D, R, T, VY, S, TX, TY)::PF, STN_G(D, R, T, VY, S, TX, TY)::PADIN,                       \
+     STN_G(D, R, T, VY, S, TX, TY)::SMEM,                                                             \
      reinterpret_cast<const void *>(&stn::sweep_kernel<D, R, T, VY, S, TX, TY>),                     \
      reinterpret_cast<const void *>(&stn::sweep_persistent<D, R, T, VY, S, TX, TY>)}

@@ -74,7 +74,11 @@ struct Registry {
                            stn::list_3d_bf16_r1, stn::list_3d_bf16_r2, stn::list_3d_bf16_r3,
                            stn::list_3d_bf16_r4, stn::list_2d_f16_r1,  stn::list_2d_f16_r2,
                            stn::list_2d_f16_r3,  stn::list_2d_f16_r4,  stn::list_3d_f16_r1,
-                           stn::list_3d_f16_r2,  stn::list_3d_f16_r3,  stn::list_3d_f16_r4};
+                           stn::list_3d_f16_r2,  stn::list_3d_f16_r3,  stn::list_3d_f16_r4,
+                           stn::list_2d_f32_r5,  stn::list_2d_f32_r6,  stn::list_3d_f32_r5,
+                           stn::list_3d_f32_r6,  stn::list_2d_bf16_r5, stn::list_2d_bf16_r6,
+                           stn::list_3d_bf16_r5, stn::list_3d_bf16_r6, stn::list_2d_f16_r5,
+                           stn::list_2d_f16_r6,  stn::list_3d_f16_r5,  stn::list_3d_f16_r6};
         for (L f : lists) {
             const stn::KernelEntry *e = nullptr;
             const int n = f(&e);
@@ -171,6 +175,7 @@ struct Pass {
     const void *fn = nullptr;
     int t = 0;
     int occ = 0;   // resident blocks per SM
+    int padin = 0; // input-plane x padding per side: 3D tensor-map box width 4*block.x + 2*padin
     dim3 grid, block;
     size_t smem = 0;
     stn::SweepArgs a{};
@@ -190,7 +195,7 @@ void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz,
     stencil_schedule d{};
     d.kernel = stream_applicable(dtype, nx) ? STENCIL_KERNEL_STREAM : STENCIL_KERNEL_NAIVE;
     if (h->dim == 2) {
-        static const int t2[5] = {0, 5, 3, 2, 2};
+        static const int t2[stn::kMaxR + 1] = {0, 5, 3, 2, 2, 2, 2};
         d.t = std::min(t2[h->r], reg.max_t(2, h->r, dtype, 1));
         d.threads_x = 128;
         d.threads_y = 1;
@@ -228,10 +233,16 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
     const int64_t tiles = ntx * nty;
     const int64_t slots = static_cast<int64_t>(dev.sms) * occ;
     const int64_t minseg = std::max<int64_t>(64, 8 * t * (2 * R + 1));
-    // 2D: the strips laid end to end hold W rows, block b sweeps [b*seg, (b+1)*seg) of
-    // them.  3D: slabs of seg planes, the tiles of one slab in consecutive blocks (their
-    // boxes overlap by the halo; neighbours that run together share those reads in L2).
-    const bool flat = D == 2;
+    // Two block orders.  Slabs: the stream axis is cut into slabs of seg planes,
+    // the tiles of one slab in consecutive blocks, so blocks that run together
+    // read neighbouring tiles of the same rows/planes (DRAM locality, shared halo
+    // reads in L2).  Strips end to end (2D kernels that are issue-bound: a long
+    // loop body, or t >= 5): the strips' rows laid end to end are split into equal
+    // ranges, one per resident block slot for long bodies, so no SM waits on a
+    // partly filled last wave.  (Measured on 16384^2: slabs win at t <= 4 with
+    // short bodies by 4-10 %, strips win by 3-25 % otherwise.)
+    const int64_t body = static_cast<int64_t>(2 * R + 1) * t * 4 * (4 * R + 1);
+    const bool flat = D == 2 && (body > 400 || t >= 5);
     const int64_t W = tiles * ns;
     int64_t seg = s.seg;
     if (seg <= 0) {
@@ -243,14 +254,8 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
             // other grids fill the device: segments long against the pipeline fill
             seg = std::max<int64_t>((W + 4 * slots - 1) / (4 * slots), minseg);
         } else {
-            // Equal blocks, one per resident block slot: no SM waits on a partly filled
-            // last wave.  Kernels with a short unrolled body (queue period x levels x
-            // cells x FMA <= 400) run better as several equal waves of ~200-row blocks,
-            // which keeps blocks out of phase; long bodies lose instruction-cache hits
-            // when blocks on one SM run different phases (prologue/steady), so they
-            // keep one wave.
             seg = (W + slots - 1) / slots;
-            const int64_t body = static_cast<int64_t>(2 * R + 1) * t * 4 * (4 * R + 1);
+            // short bodies: several equal waves of ~200-row blocks keep blocks out of phase
             if (body <= 400) seg = std::min<int64_t>(seg, std::max<int64_t>(192, (W + 8 * slots - 1) / (8 * slots)));
         }
     }
@@ -265,6 +270,7 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
     ps.grid = dim3(static_cast<unsigned>(nblk));
     ps.block = dim3(e->tx, e->ty);
     ps.smem = e->smem;
+    ps.padin = e->padin;
     stn::SweepArgs &a = ps.a;
     a.nx = static_cast<int>(nx);
     a.ny = static_cast<int>(ny);
@@ -440,8 +446,7 @@ int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny,
             CUtensorMap map;
             std::memset(&map, 0, sizeof(map));
             if (h->dim == 3) {
-                const int pad = dtype == STENCIL_F32 ? 4 : 8;
-                rc = encode_map(&map, src, nx, ny, nz, dtype, 4 * static_cast<int>(ps.block.x) + 2 * pad,
+                rc = encode_map(&map, src, nx, ny, nz, dtype, 4 * static_cast<int>(ps.block.x) + 2 * ps.padin,
                                 static_cast<int>(ps.block.y) * s.rows_per_thread + 2 * h->r);
                 if (rc) return rc;
             }
@@ -675,8 +680,7 @@ int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cuda
                 CUtensorMap m;
                 std::memset(&m, 0, sizeof(m));
                 if (b.h->dim == 3) {
-                    const int pad = b.dtype == STENCIL_F32 ? 4 : 8;
-                    int rc = encode_map(&m, src, b.nx, b.ny, b.nz, b.dtype, 4 * kind->tx + 2 * pad,
+                    int rc = encode_map(&m, src, b.nx, b.ny, b.nz, b.dtype, 4 * kind->tx + 2 * kind->padin,
                                         kind->ty * x->rows + 2 * b.h->r);
                     if (rc) return rc;
                 }
@@ -798,7 +802,7 @@ int stencil_create(stencil_handle *out, int dim, int radius, const float *coeffs
 {
     if (!out || !coeffs) return STENCIL_ERR_INVALID_ARG;
     *out = nullptr;
-    if ((dim != 2 && dim != 3) || radius < 1 || radius > 4) return STENCIL_ERR_INVALID_ARG;
+    if ((dim != 2 && dim != 3) || radius < 1 || radius > stn::kMaxR) return STENCIL_ERR_INVALID_ARG;
     stencil_plan *h = new (std::nothrow) stencil_plan;
     if (!h) return STENCIL_ERR_OOM;
     h->dim = dim;
@@ -957,8 +961,7 @@ int stencil_run_noalloc(stencil_handle h, const void *in, void *out, int64_t nx,
             CUtensorMap map;
             std::memset(&map, 0, sizeof(map));
             if (h->dim == 3) {
-                const int pad = dtype == STENCIL_F32 ? 4 : 8;
-                rc = encode_map(&map, src, nx, ny, nz, dtype, 4 * static_cast<int>(ps.block.x) + 2 * pad,
+                rc = encode_map(&map, src, nx, ny, nz, dtype, 4 * static_cast<int>(ps.block.x) + 2 * ps.padin,
                                 static_cast<int>(ps.block.y) * s.rows_per_thread + 2 * h->r);
                 if (rc) return rc;
             }

@@ -1,0 +1,18 @@
+// Streaming-kernel instantiations: radius 5, float storage;
+// 2D, 128 threads x 4 cells per block row, temporal degrees 1..3.
+#include "registry.h"
+#include "sweep_kernel.cuh"
+
+namespace stn {
+namespace {
+const KernelEntry kList[] = {
+    STN_E(2, 5, 1, 1, float, 0, 128, 1),
+    STN_E(2, 5, 2, 1, float, 0, 128, 1),
+    STN_E(2, 5, 3, 1, float, 0, 128, 1)};
+}  // namespace
+int list_2d_f32_r5(const KernelEntry **e)
+{
+    *e = kList;
+    return static_cast<int>(sizeof(kList) / sizeof(kList[0]));
+}
+}  // namespace stn

@@ -5,7 +5,8 @@
 
 namespace stn {
 
-constexpr int kMaxK = 25;            // 2*3*4 + 1 coefficients
+constexpr int kMaxR = 6;             // largest radius
+constexpr int kMaxK = 2 * 3 * kMaxR + 1;   // coefficients of a 3D radius-6 stencil
 constexpr int kSmemHeader = 1024;    // mbarriers + abort flag
 constexpr int kMaxDepthIn = 64;
 constexpr unsigned kStatusTimeout = 1u;
@@ -23,14 +24,17 @@ __host__ __device__ constexpr int rup(int a, int b) { return cdiv(a, b) * b; }
 template <int D, int R, int T, int VY, int ES, int TX, int TY> struct Geo {
     static constexpr int QP = 2 * R + 1;               // register-queue period
     static constexpr bool F32S = ES == 4;
-    static constexpr int PADIN = 16 / ES;              // input row padding (elements)
+    static constexpr int NV = cdiv(R, 4);              // 4-cell vectors of x neighbours per side
+    static constexpr int ALIGN = 16 / ES;              // cells per 16 bytes of storage
+    static constexpr int PADIN = ALIGN > 4 * NV ? ALIGN : 4 * NV;   // input row padding (cells)
+    static constexpr int PAD32 = 4 * NV;               // FP32 ring row padding (cells)
     static constexpr int BX = 4 * TX;                  // thread-region width (cells)
     static constexpr int BY = (D == 3) ? TY * VY : 1;  // thread-region rows (3D)
-    static constexpr int HTX = rup((T - 1) * R, PADIN);   // x halo of levels 1..T (16-byte multiple)
+    static constexpr int HTX = rup((T - 1) * R, ALIGN);   // x halo of levels 1..T (16-byte multiple)
     static constexpr int HTY = (D == 3) ? (T - 1) * R : 0;
     static constexpr int CX = BX - 2 * HTX;            // compute tile (Eq. 2: bsize - 2 t r)
     static constexpr int CY = (D == 3) ? BY - 2 * HTY : 1;
-    static constexpr int PW = BX + 8;                  // FP32 plane row: 4 pad cells either side
+    static constexpr int PW = BX + 2 * PAD32;          // FP32 plane row: PAD32 pad cells either side
     static constexpr int PH = (D == 3) ? BY + 2 * R : 1;
     static constexpr int PWIN = BX + 2 * PADIN;        // input plane row (elements)
     static constexpr int SLOT32 = rup(PW * PH, 32);    // floats per FP32 ring slot

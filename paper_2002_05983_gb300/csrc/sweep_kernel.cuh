@@ -216,9 +216,12 @@ __host__ __device__ constexpr int cmod(int a, int m) { return ((a % m) + m) % m;
 __host__ __device__ constexpr int cclamp(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
 
 // ------------------------------------------------------- ghost (clamp) fill
-// Tasks that overwrite the out-of-grid frame (width <= 4 in x, r in y) of a
-// padded plane with clamped border values, in groups of four cells.
-struct Ghost {
+// 2D kernels of radius <= 4 (one-vector x frame) keep this loop form of the
+// frame fill: the per-thread plans below measured 3-7 % slower there (code
+// layout of the unrolled body), while they are 9-22 % faster in 3D.
+// Tasks that overwrite the out-of-grid frame (width 4 in x) of a padded plane
+// with clamped border values, in groups of four cells.
+struct GhostX4 {
     int ntask, nA, nc;      // total tasks, column tasks, columns per in-grid row (0..2)
     int rA0;                // first in-grid padded row
     int cL, cR;             // padded float4 columns at x = -4 and x = nx (or -1)
@@ -228,9 +231,9 @@ struct Ghost {
     int cg0, ncg;           // float4 columns of the ghost rows
 };
 
-__device__ __forceinline__ Ghost make_ghost(int ox, int oy, int pw, int ph, int nx, int nyp, int r)
+__device__ __forceinline__ GhostX4 make_ghost_x4(int ox, int oy, int pw, int ph, int nx, int nyp, int r)
 {
-    Ghost g;
+    GhostX4 g;
     const int xL = -4 - ox, xR = nx - ox;
     g.cL = (xL >= 0 && xL + 4 <= pw) ? xL / 4 : -1;
     g.cR = (xR >= 0 && xR + 4 <= pw) ? xR / 4 : -1;
@@ -258,7 +261,7 @@ __device__ __forceinline__ Ghost make_ghost(int ox, int oy, int pw, int ph, int 
 // Cells are moved as raw bits, four at a time: 4-byte cells (FP32 rings, FP32
 // input) or 2-byte cells (BF16/FP16 input).
 template <int ES>
-__device__ __forceinline__ void ghost_fill(void *plane_, const Ghost &g, int pw, int ox, int nx, int tid, int nthr)
+__device__ __forceinline__ void ghost_fill_x4(void *plane_, const GhostX4 &g, int pw, int ox, int nx, int tid, int nthr)
 {
     using W = typename std::conditional<ES == 4, uint32_t, uint16_t>::type;
     using V = typename std::conditional<ES == 4, uint4, uint2>::type;
@@ -295,6 +298,118 @@ __device__ __forceinline__ void ghost_fill(void *plane_, const Ghost &g, int pw,
     }
 }
 
+// Tasks that overwrite the out-of-grid frame (fw = 4*nv cells in x, r rows in
+// y) of a padded plane with clamped border values, in groups of four cells.
+struct Ghost {
+    int ntask, nA, nc;      // total tasks, column tasks, frame columns per in-grid row
+    int rA0;                // first in-grid padded row
+    int cL0, nL, cR0;       // left frame: nL 4-cell columns from cL0; right frame from cR0
+    int srcL, srcR;         // padded x of global x = 0 and x = nx-1
+    int rT0, nT, srcT;      // top ghost rows, their count, padded source row
+    int rB0, nB, srcB;      // bottom ghost rows
+    int cg0, ncg;           // 4-cell columns of the ghost rows
+};
+
+__device__ __forceinline__ Ghost make_ghost(int ox, int oy, int pw, int ph, int nx, int nyp, int r, int fw)
+{
+    Ghost g;
+    // left frame x in [-fw, 0), right frame x in [nx, nx + fw), clipped to the plane
+    const int l0 = max(-fw - ox, 0), l1 = min(-ox, pw);
+    const int q0 = max(nx - ox, 0), q1 = min(nx + fw - ox, pw);
+    g.cL0 = l0 / 4;
+    g.nL = l1 > l0 ? (l1 - l0) / 4 : 0;
+    g.cR0 = q0 / 4;
+    const int nR = q1 > q0 ? (q1 - q0) / 4 : 0;
+    g.srcL = -ox;
+    g.srcR = nx - 1 - ox;
+    g.nc = g.nL + nR;
+    const int a0 = max(0, oy), a1 = min(nyp, oy + ph);
+    g.rA0 = a0 - oy;
+    g.nA = (a1 > a0 ? a1 - a0 : 0) * g.nc;
+    const int t0 = max(-r, oy), t1 = min(0, oy + ph);
+    g.rT0 = t0 - oy;
+    g.nT = t1 > t0 ? t1 - t0 : 0;
+    g.srcT = -oy;
+    const int b0 = max(nyp, oy), b1 = min(nyp + r, oy + ph);
+    g.rB0 = b0 - oy;
+    g.nB = b1 > b0 ? b1 - b0 : 0;
+    g.srcB = nyp - 1 - oy;
+    const int x0 = max(-fw, ox), x1 = min(nx + fw, ox + pw);
+    g.cg0 = (x0 - ox) / 4;
+    g.ncg = x1 > x0 ? (x1 - x0) / 4 : 0;
+    g.ntask = g.nA + (g.nT + g.nB) * g.ncg;
+    return g;
+}
+
+// Each thread's share of the frame tasks, resolved once per tile: task j moves
+// four cells to cell offset dst[j] (< 0: none), from offset src[j] (four cells)
+// or, for src[j] < 0, the single cell -src[j]-1 broadcast (clamp).
+template <int MAXT> struct GhostPlan {
+    int dst[MAXT], src[MAXT];
+};
+
+template <int MAXT>
+__device__ __forceinline__ GhostPlan<MAXT> plan_ghost(const Ghost &g, int pw, int ox, int nx, int tid, int nthr)
+{
+    GhostPlan<MAXT> p;
+#pragma unroll
+    for (int j = 0; j < MAXT; ++j) {
+        const int t = tid + j * nthr;
+        p.dst[j] = -1;
+        p.src[j] = 0;
+        if (t >= g.ntask) continue;
+        int row, col, src;
+        if (t < g.nA) {
+            row = g.rA0 + t / g.nc;
+            const int c = t % g.nc;
+            const bool left = c < g.nL;
+            col = left ? g.cL0 + c : g.cR0 + (c - g.nL);
+            src = -(row * pw + (left ? g.srcL : g.srcR)) - 1;
+        } else {
+            const int u = t - g.nA;
+            const int gr = u / g.ncg;
+            col = g.cg0 + u % g.ncg;
+            int srow;
+            if (gr < g.nT) { row = g.rT0 + gr; srow = g.srcT; }
+            else { row = g.rB0 + gr - g.nT; srow = g.srcB; }
+            const int x4 = ox + 4 * col;
+            if (x4 < 0) src = -(srow * pw + g.srcL) - 1;
+            else if (x4 >= nx) src = -(srow * pw + g.srcR) - 1;
+            else src = srow * pw + 4 * col;
+        }
+        p.dst[j] = row * pw + 4 * col;
+        p.src[j] = src;
+    }
+    return p;
+}
+
+// Cells are moved as raw bits: 4-byte cells (FP32 rings, FP32 input) or 2-byte
+// cells (BF16/FP16 input).  Branch-free: a broadcast reads the same cell four
+// times (stride 0), a copy four neighbouring cells (stride 1).
+template <int ES, int MAXT>
+__device__ __forceinline__ void ghost_apply(void *plane_, const GhostPlan<MAXT> &p)
+{
+    using W = typename std::conditional<ES == 4, uint32_t, uint16_t>::type;
+    W *plane = static_cast<W *>(plane_);
+#pragma unroll
+    for (int j = 0; j < MAXT; ++j) {
+        if (p.dst[j] < 0) continue;
+        const int bc = p.src[j] < 0;
+        const W *sp = plane + (bc ? -p.src[j] - 1 : p.src[j]);
+        const int st = bc ? 0 : 1;
+        W e[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) e[c] = sp[c * st];
+        if constexpr (ES == 4) {
+            *reinterpret_cast<uint4 *>(plane + p.dst[j]) = make_uint4(e[0], e[1], e[2], e[3]);
+        } else {
+            *reinterpret_cast<uint2 *>(plane + p.dst[j]) =
+                make_uint2(static_cast<uint32_t>(e[0]) | (static_cast<uint32_t>(e[1]) << 16),
+                           static_cast<uint32_t>(e[2]) | (static_cast<uint32_t>(e[3]) << 16));
+        }
+    }
+}
+
 __device__ __forceinline__ void mbar_inval(uint32_t bar)
 {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
@@ -311,7 +426,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
 {
     using G = Geo<D, R, T, VY, static_cast<int>(sizeof(S)), TX, TY>;
     static_assert(D == 2 || D == 3, "dim");
-    static_assert(R >= 1 && R <= 4, "radius");
+    static_assert(R >= 1 && R <= kMaxR, "radius");
     static_assert(D == 3 || (VY == 1 && TY == 1), "2D keeps one row per thread");
     static_assert(G::OK, "tile too small for this temporal degree");
     constexpr int QP = G::QP;
@@ -352,7 +467,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     const int tile_y = (D == 3) ? col / a.ntx : 0;
     const int gx0 = tile_x * G::CX - G::HTX;          // thread-region origin
     const int gy0 = (D == 3) ? tile_y * G::CY - G::HTY : 0;
-    const int ox = gx0 - 4;                            // padded FP32 plane origin
+    const int ox = gx0 - G::PAD32;                     // padded FP32 plane origin
     const int oy = (D == 3) ? gy0 - R : 0;
     const int ox_in = gx0 - PADIN;                     // padded input plane origin
     const int last = a.ns - 1;
@@ -361,7 +476,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     const int xl = 4 * tx;
     const int yl0 = ty * VY;
     const int prow0 = (D == 3) ? yl0 + R : 0;          // padded row of own row 0
-    const int toff = prow0 * PW + xl + 4;              // own cell 0 in an FP32 plane
+    const int toff = prow0 * PW + xl + G::PAD32;       // own cell 0 in an FP32 plane
     const int toffin = prow0 * PWIN + xl + PADIN;      // own cell 0 in an input plane
     const int gx = gx0 + xl;
     const bool xstore = xl >= G::HTX && xl < G::HTX + G::CX && gx < a.nx;
@@ -415,8 +530,32 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     const int lmax = min(hi[0], last);                 // last input plane to load
     const int lap0 = k0 / DEPTH;
 
-    const Ghost gh = make_ghost(ox, oy, PW, G::PH, a.nx, (D == 3) ? a.ny : 1, R);   // FP32 rings
-    const Ghost gh_in = F32S ? gh : make_ghost(ox_in, oy, PWIN, G::PH, a.nx, (D == 3) ? a.ny : 1, R);
+    // clamp frames (x: the 4*NV cells the neighbour loads reach; 3D y: r rows) of the
+    // FP32 rings and of the input ring, each thread's tasks resolved once per tile
+    constexpr int FW = 4 * G::NV;
+    constexpr bool SAME = F32S && G::PADIN == G::PAD32;   // input ring laid out like the FP32 rings
+    constexpr int MT32 = cdiv((D == 3) ? G::PH * 2 * G::NV + 2 * R * (PW / 4) : 2 * G::NV, NTHR);
+    constexpr int MTIN = cdiv((D == 3) ? G::PH * 2 * G::NV + 2 * R * (PWIN / 4) : 2 * G::NV, NTHR);
+    constexpr bool X4 = D == 2 && G::NV == 1;          // loop-form fill (GhostX4)
+    const Ghost g32 = make_ghost(ox, oy, PW, G::PH, a.nx, (D == 3) ? a.ny : 1, R, FW);
+    const bool gh_on = g32.ntask > 0;                  // block-uniform: tile touches an x or y edge
+    GhostPlan<X4 ? 1 : MT32> gp32;
+    GhostPlan<(X4 || SAME) ? 1 : MTIN> gpin;
+    GhostX4 gx32, gxin;
+    if constexpr (X4) {
+        gx32 = make_ghost_x4(ox, oy, PW, G::PH, a.nx, 1, R);
+        gxin = F32S ? gx32 : make_ghost_x4(ox_in, oy, PWIN, G::PH, a.nx, 1, R);
+    } else {
+        gp32 = plan_ghost<MT32>(g32, PW, ox, a.nx, tid, NTHR);
+        if constexpr (!SAME) {
+            const Ghost gin = make_ghost(ox_in, oy, PWIN, G::PH, a.nx, (D == 3) ? a.ny : 1, R, FW);
+            gpin = plan_ghost<MTIN>(gin, PWIN, ox_in, a.nx, tid, NTHR);
+        }
+    }
+    (void)gp32;
+    (void)gpin;
+    (void)gx32;
+    (void)gxin;
 
     if (tid == 0) {
         for (int i = 0; i < DEPTH; ++i) mbar_init(smem_addr(bars + i), 1);
@@ -546,12 +685,17 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                 ld(VY + m, 0, dn[m]);
             }
         }
+        constexpr int NV = G::NV;
         float res[VY][4];
 #pragma unroll
         for (int vy = 0; vy < VY; ++vy) {
-            float L[4], Rr[4];
-            ld(vy, -4, L);
-            ld(vy, 4, Rr);
+            // L[m] holds cells x0-4(m+1) .. x0-4m-1, Rr[m] cells x0+4(m+1) .. x0+4m+7
+            float L[NV][4], Rr[NV][4];
+#pragma unroll
+            for (int m = 0; m < NV; ++m) {
+                ld(vy, -4 * (m + 1), L[m]);
+                ld(vy, 4 * (m + 1), Rr[m]);
+            }
             const float(&ctr)[VY][4] = q[s - 1][jc];
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
@@ -559,8 +703,10 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
 #pragma unroll
                 for (int i = 1; i <= R; ++i) {
                     const int cb = 1 + (i - 1) * K2;
-                    const float w = (v - i >= 0) ? ctr[vy][cclamp(v - i, 0, 3)] : L[cclamp(4 + v - i, 0, 3)];
-                    const float e = (v + i <= 3) ? ctr[vy][cclamp(v + i, 0, 3)] : Rr[cclamp(v + i - 4, 0, 3)];
+                    const float w = (v - i >= 0) ? ctr[vy][cclamp(v - i, 0, 3)]
+                                                 : L[cclamp((i - v - 1) / 4, 0, NV - 1)][cclamp(v - i + 4 * ((i - v - 1) / 4 + 1), 0, 3)];
+                    const float e = (v + i <= 3) ? ctr[vy][cclamp(v + i, 0, 3)]
+                                                 : Rr[cclamp((v + i) / 4 - 1, 0, NV - 1)][cclamp((v + i) % 4, 0, 3)];
                     acc = __fmaf_rn(cf[cb + 0], w, acc);
                     acc = __fmaf_rn(cf[cb + 1], e, acc);
                     if constexpr (D == 3) {
@@ -646,7 +792,11 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
             }
         }
         // the input slot is level 0's ring: clamp its out-of-grid frame now (read from step k+1 on)
-        if (gh_in.ntask > 0) ghost_fill<sizeof(S)>(inslot + J * SLOTIN, gh_in, PWIN, ox_in, a.nx, tid, NTHR);
+        if (gh_on) {
+            if constexpr (X4) ghost_fill_x4<sizeof(S)>(inslot + J * SLOTIN, gxin, PWIN, ox_in, a.nx, tid, NTHR);
+            else if constexpr (SAME) ghost_apply<sizeof(S)>(inslot + J * SLOTIN, gp32);
+            else ghost_apply<sizeof(S)>(inslot + J * SLOTIN, gpin);
+        }
     };
 
     // ---- one step
@@ -662,7 +812,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         if (tid == 0) {
             const int qn = k + G::PF;
             if (qn <= lmax) {
-                if (gh_in.ntask > 0) fence_proxy_async_smem();
+                if (gh_on) fence_proxy_async_smem();
                 issue(qn);
             }
         }
@@ -674,12 +824,15 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         level0(Jc, CKc, k);
         level(IC<1>{}, Jc, CKc, k);
         // clamp frame of ring planes written in the previous step
-        if (gh.ntask > 0) {
+        if (gh_on) {
             SFor<1, T>::run([&](auto sc) {
                 constexpr int s = decltype(sc)::value;
                 const int p = k - 1 - G::lag(s);
                 if (p >= lo[s] && p <= min(hi[s], last))
-                    ghost_fill<4>(ring32(s, rslot(s, J, 1)), gh, PW, ox, a.nx, tid, NTHR);
+                {
+                    if constexpr (X4) ghost_fill_x4<4>(ring32(s, rslot(s, J, 1)), gx32, PW, ox, a.nx, tid, NTHR);
+                    else ghost_apply<4>(ring32(s, rslot(s, J, 1)), gp32);
+                }
             });
         }
         __syncthreads();

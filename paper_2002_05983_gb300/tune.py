@@ -92,6 +92,13 @@ def regret(model, measured):
     return res
 
 
+def analytic_accuracy(measured):
+    """Measured / analytic-predicted time per cell update, every timed schedule (the
+    model-accuracy ratio the paper reports per configuration)."""
+    return np.array([t.ns_per_cell / t.analytic_ns_per_cell for _, rows in measured for t in rows
+                     if t.ns_per_cell > 0 and t.analytic_ns_per_cell > 0], np.float64)
+
+
 def evaluate(n_train=48, n_test=16, seed=3, epochs=3000):
     """Measure, train on the first n_train problems, report regret on the rest."""
     probs = tuning_problems(n_train + n_test, seed)
@@ -104,4 +111,4 @@ def evaluate(n_train=48, n_test=16, seed=3, epochs=3000):
     finally:
         stencil_model_destroy(model)
     return dict(rows_train=int(len(y)), rows_total=int(sum(len(r) for _, r in meas)), train_loss=loss,
-                test=test, train=train_r)
+                test=test, train=train_r, analytic_ratio=analytic_accuracy(meas))

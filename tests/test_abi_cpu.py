@@ -41,7 +41,7 @@ def test_strerror_and_codes(lib):
 
 def test_create_validates_on_host(lib):
     c = np.ones(5, np.float32)
-    for dim, r in ((1, 1), (4, 1), (2, 0), (2, 5)):
+    for dim, r in ((1, 1), (4, 1), (2, 0), (2, 7), (3, 7)):
         with pytest.raises(st.StencilError) as e:
             st.stencil_create(dim, r, c)
         assert e.value.code == st.STENCIL_ERR_INVALID_ARG
@@ -82,6 +82,9 @@ def test_compiled_temporal_degrees(lib):
     assert st.stencil_max_t(2, 1, 0) == 16
     assert [st.stencil_max_t(2, r, 0) for r in (2, 3, 4)] == [8, 6, 4]
     assert [st.stencil_max_t(3, r, 0, 2) for r in (1, 2, 3, 4)] == [6, 4, 2, 2]
+    # radius 5 and 6 (beyond the paper's 1..4): 2D t = 1..3, 3D t = 1 with 2 or 4 rows
+    assert [st.stencil_max_t(2, r, dt) for r in (5, 6) for dt in (0, 1, 2)] == [3] * 6
+    assert [st.stencil_max_t(3, r, 0, vy) for r in (5, 6) for vy in (2, 4)] == [1] * 4
     for dt in (1, 2):
         assert st.stencil_max_t(2, 1, dt) == 16
 

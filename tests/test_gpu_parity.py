@@ -38,7 +38,7 @@ def test_smoke_config_2d_r1_256():
         assert np.max(np.abs(got.numpy() - want64)) <= 2e-6 * 10
 
 
-CASES_2D = [(r, t) for r in (1, 2, 3, 4) for t in sorted({1, 2, 3, st.stencil_max_t(2, r, 0)})]
+CASES_2D = [(r, t) for r in (1, 2, 3, 4, 5, 6) for t in sorted({1, 2, 3, st.stencil_max_t(2, r, 0)})]
 
 
 @pytest.mark.parametrize("r,t", CASES_2D)
@@ -56,7 +56,7 @@ def test_2d_stream_bit_exact(r, t):
     assert np.max(np.abs(got.numpy() - w64)) <= 2e-6 * iters
 
 
-CASES_3D = [(r, t, vy) for r in (1, 2, 3, 4) for vy in (2, 4)
+CASES_3D = [(r, t, vy) for r in (1, 2, 3, 4, 5, 6) for vy in (2, 4)
             for t in sorted({1, st.stencil_max_t(3, r, 0, vy)})]
 
 
@@ -72,7 +72,7 @@ def test_3d_stream_bit_exact(r, t, vy):
     assert_bits_equal(got, want, f"3D r={r} t={t} vy={vy}")
 
 
-@pytest.mark.parametrize("dim,r", [(2, 1), (2, 4), (3, 1), (3, 3)])
+@pytest.mark.parametrize("dim,r", [(2, 1), (2, 4), (2, 6), (3, 1), (3, 3), (3, 5)])
 def test_schedules_bit_identical_to_naive(dim, r):
     """Every FP32 schedule equals the one-thread-per-cell t=1 schedule bit for bit."""
     shape = (300, 260) if dim == 2 else (40, 36, 44)
@@ -98,13 +98,14 @@ def test_schedules_bit_identical_to_naive(dim, r):
 
 @pytest.mark.parametrize("dim,shape,r", [
     (2, (1, 4), 1), (2, (3, 8), 4), (2, (64, 4), 3), (2, (5, 1000), 2),
-    (3, (1, 1, 4), 2), (3, (3, 5, 8), 4), (3, (9, 2, 12), 1), (3, (2, 40, 8), 3)])
+    (3, (1, 1, 4), 2), (3, (3, 5, 8), 4), (3, (9, 2, 12), 1), (3, (2, 40, 8), 3),
+    (2, (7, 12), 6), (3, (4, 9, 16), 5)])
 def test_tiny_and_degenerate_grids(dim, shape, r):
     """Sides smaller than the radius, single rows/planes: clamp everywhere."""
     f = gen.uniform_grid(shape, seed=5)
     c = gen.coefficients(dim, r)
     s = st.Stencil(dim, r, c)
-    for t in (1, 2):
+    for t in sorted({1, min(2, st.stencil_max_t(dim, r, 0))}):
         want = oracle.sweep_f32(f, dim, r, c, 5)
         got = run_gpu(s, torch.from_numpy(f), 5, kernel=st.KERNEL_STREAM, t=t)
         assert_bits_equal(got, want, f"tiny {shape} t={t}")

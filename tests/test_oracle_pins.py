@@ -92,7 +92,8 @@ def run_f64(oracle_mod, f, dim, r, c, iters):
 # ---------------------------------------------------------------- pins
 @pytest.mark.parametrize("dim,nx,ny,nz,r", [
     (2, 5, 7, 1, 1), (2, 5, 7, 1, 2), (2, 5, 7, 1, 4), (2, 3, 2, 1, 3),
-    (3, 3, 4, 5, 1), (3, 3, 4, 5, 2), (3, 4, 3, 2, 4), (3, 1, 2, 3, 2)])
+    (3, 3, 4, 5, 1), (3, 3, 4, 5, 2), (3, 4, 3, 2, 4), (3, 1, 2, 3, 2),
+    (2, 9, 8, 1, 6), (3, 4, 5, 3, 5)])
 def test_dense_operator_power(oracle_mod, dim, nx, ny, nz, r):
     """A^iters x (dense operator, clamp folded in) equals the FP64 oracle."""
     rng = np.random.default_rng(100 + dim * 10 + r)
@@ -117,7 +118,7 @@ def test_dense_operator_random_signed_coeffs(oracle_mod, dim, r):
     np.testing.assert_allclose(run_f64(oracle_mod, f, dim, r, c, 3), ref, rtol=1e-12, atol=1e-12)
 
 
-@pytest.mark.parametrize("dim,r", [(2, 1), (2, 2), (2, 4), (3, 1), (3, 3), (3, 4)])
+@pytest.mark.parametrize("dim,r", [(2, 1), (2, 2), (2, 4), (3, 1), (3, 3), (3, 4), (2, 6), (3, 5)])
 def test_shift_stencil_exact(oracle_mod, dim, r):
     """A single unit coefficient at (distance i, direction d) moves the field by
     i*iters cells against that direction, clamped: out[p] = in[clamp(p + i*iters*e_d)].
