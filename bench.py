@@ -319,6 +319,33 @@ def suite_main(args):
                  max_abs_vs_fp64=float(np.max(np.abs(got - w64))), bound=2e-6 * iters)
         return 0
 
+    if args.suite == "shared":
+        # one coefficient per distance vs one per (distance, direction), default schedules
+        for dim, shape, iters, side in ((2, (16384, 16384), 1000, 1024), (3, (512, 512, 512), 200, 128)):
+            x = _rand(shape, f32, 0)
+            out = torch.empty_like(x)
+            n = x.numel()
+            for r in RADII:
+                full = st.Stencil(dim, r, gen.coefficients(dim, r))
+                sh = st.Stencil(dim, r, gen.shared_coefficients(dim, r), shared=True)
+                g_full = n * iters / _timed(lambda: full.run(x, iters, out=out), reps=1) / 1e9
+                g_sh = n * iters / _timed(lambda: sh.run(x, iters, out=out), reps=1) / 1e9
+                f_sh = 1 + r * (2 * dim + 1)   # FLOP per cell update with shared coefficients
+                _row(suite="shared", dim=dim, r=r, grid=list(shape), iters=iters, t=sh.default_schedule(shape).t,
+                     gcells_shared=round(g_sh, 1), gflops_shared=round(g_sh * f_sh, 1), flop_per_cell_shared=f_sh,
+                     gcells_full=round(g_full, 1), gflops_full=round(g_full * metrics.flop_per_cell(dim, r), 1))
+            del x, out
+            f = crop_input(side) if dim == 2 else gen.workload_grid(3, side, side, side)
+            for r in RADII:
+                c = gen.shared_coefficients(dim, r)
+                got = st.Stencil(dim, r, c, shared=True).run(torch.from_numpy(f).cuda(), iters).cpu().numpy()
+                w32 = oracle.sweep_shared_f32(f, dim, r, c, iters)
+                w64 = oracle.sweep_shared_f64(f.astype(np.float64), dim, r, c.astype(np.float64), iters)
+                _row(suite="shared", parity=True, dim=dim, r=r, crop=side, iters=iters,
+                     bit_exact_vs_fp32_oracle=bool(np.array_equal(got, w32)),
+                     max_abs_vs_fp64=float(np.max(np.abs(got - w64))), bound=2e-6 * iters)
+        return 0
+
     if args.suite == "precision":
         iters = 500
         for dim, shape, small in ((3, (768, 768, 768), 128), (2, (32768, 32768), 2048)):
@@ -428,8 +455,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--suite", choices=["sweep2d", "sweep3d", "precision", "batch"], default=None,
-                    help="other workloads: t sweeps, 16-bit storage, 96-grid batch (JSON lines)")
+    ap.add_argument("--suite", choices=["sweep2d", "sweep3d", "precision", "batch", "shared"], default=None,
+                    help="other workloads: t sweeps, 16-bit storage, 96-grid batch, shared coefficients (JSON lines)")
     ap.add_argument("--radii", default="1,2,3,4",
                     help="radii of the sweep2d/sweep3d suites (1..6; the paper's range is 1..4)")
     ap.add_argument("--tune-eval", action="store_true",

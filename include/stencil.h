@@ -93,7 +93,7 @@ typedef struct {
 } stencil_schedule;
 
 /* Number of features describing one (problem, schedule) pair for the cost model. */
-#define STENCIL_NFEAT 12
+#define STENCIL_NFEAT 14
 
 /* One measured or predicted schedule of a problem (stencil_tune output). */
 typedef struct {
@@ -117,6 +117,22 @@ typedef enum {
  * (layout above; copied, the caller keeps ownership).  Allocates no device
  * memory.  Errors: INVALID_ARG. */
 int stencil_create(stencil_handle *out, int dim, int radius, const float *coeffs);
+
+/* Create a stencil with one coefficient per distance: K = radius + 1 FP32
+ * coefficients, c[0] for the centre and c[i] for every neighbour at distance
+ * i, the form of the stencils the paper compares against in Section IV.C
+ * (its Sections IV.A and V.A note that sharing removes multiplications but
+ * no additions).  Reordering is allowed there; this library fixes one order:
+ *
+ *   g(p) = c[0] f(p) + sum_{i=1..r} c[i] * s_i(p),
+ *   s_i = (((W + E) + S) + N) [+ B) + A],
+ *
+ * the 2*dim neighbours at distance i (clamped as above) summed left to right
+ * in FP32, then one FMA per distance (FP32 path: one rounded multiply, then per
+ * distance 2*dim-1 rounded adds and one FMA).  Streaming kernels exist for FP32
+ * storage, radius 1..4; other cases run the one-step-per-launch kernel.
+ * Errors: INVALID_ARG. */
+int stencil_create_shared(stencil_handle *out, int dim, int radius, const float *coeffs);
 
 /* Free the handle and its scratch grid.  Synchronises the device first so
  * that no enqueued run still uses the scratch grid.  NULL is accepted. */
@@ -175,7 +191,9 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
  * log2 ny, log2 nz, bytes per element, t, resident warps per SM, tile height
  * (rows, 1 in 2D), log2 of the unrolled loop body's FMA count
  * ((2r+1) * t * 4 * rows * (2*dim*r+1)), log2 segment length, log2 analytic
- * ns per cell update.  `sched` may be partial (0 = library choice). */
+ * ns per cell update, block order (1: 2D strips laid end to end, 0: slabs),
+ * log2 of the launch's blocks per resident block slot (waves).  `sched` may
+ * be partial (0 = library choice). */
 int stencil_schedule_features(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
                               const stencil_schedule *sched, float *features);
 

@@ -50,7 +50,7 @@ def _load():
             lib = ctypes.CDLL(_LIB)
             i64, i32 = ctypes.c_int64, ctypes.c_int
             vp = ctypes.c_void_p
-            for name in ("oracle_sweep_f64", "oracle_sweep_f32"):
+            for name in ("oracle_sweep_f64", "oracle_sweep_f32", "oracle_sweep_shared_f64", "oracle_sweep_shared_f32"):
                 fn = getattr(lib, name)
                 fn.argtypes = [vp, vp, i64, i64, i64, i32, i32, vp, i32, i32]
                 fn.restype = i32
@@ -103,3 +103,27 @@ def sweep_f32(grid, dim: int, radius: int, coeffs, iters: int, threads: int = 0)
     if rc:
         raise RuntimeError(f"oracle_sweep_f32 failed ({rc})")
     return out
+
+
+def _sweep(fn: str, grid, dim: int, radius: int, coeffs, iters: int, threads: int, dtype, k: int):
+    lib = _load()
+    f = np.ascontiguousarray(grid, dtype=dtype)
+    c = np.ascontiguousarray(coeffs, dtype=dtype)
+    if c.size != k:
+        raise ValueError(f"need {k} coefficients")
+    out = np.empty_like(f)
+    nx, ny, nz = _dims(f, dim)
+    rc = getattr(lib, fn)(f.ctypes.data, out.ctypes.data, nx, ny, nz, dim, radius, c.ctypes.data, iters, threads)
+    if rc:
+        raise RuntimeError(f"{fn} failed ({rc})")
+    return out
+
+
+def sweep_shared_f64(grid, dim: int, radius: int, coeffs, iters: int, threads: int = 0) -> np.ndarray:
+    """`iters` FP64 steps of the shared-coefficient form (c[0..r], one per distance)."""
+    return _sweep("oracle_sweep_shared_f64", grid, dim, radius, coeffs, iters, threads, np.float64, radius + 1)
+
+
+def sweep_shared_f32(grid, dim: int, radius: int, coeffs, iters: int, threads: int = 0) -> np.ndarray:
+    """FP32 shared-coefficient steps: left-to-right neighbour sum, one fmaf per distance."""
+    return _sweep("oracle_sweep_shared_f32", grid, dim, radius, coeffs, iters, threads, np.float32, radius + 1)

@@ -35,6 +35,18 @@
  *    order -- the multiply-then-FMA chain of Section V.A (each
  *    multiplication fused with the addition that follows it).
  *
+ * Shared-coefficient form (one coefficient per distance, the stencils the
+ * paper compares against in Section IV.C; Sections IV.A and V.A note that
+ * sharing removes multiplications but not additions):
+ *
+ *   g(p) = c_0 f(p) + sum_{i=1..r} c_i * (f(W,i) + f(E,i) + f(S,i) + f(N,i) [+ f(B,i) + f(A,i)])
+ *
+ * Reordering is allowed for this form and the paper gives no order; the
+ * order here: the 2*dim neighbours at distance i summed left to right (W, E,
+ * S, N, B, A), then acc + c_i * sum.  oracle_sweep_shared_f64 uses plain
+ * double multiplies and adds; oracle_sweep_shared_f32 uses single-precision
+ * adds for the sum and one fmaf per distance.  Coefficients c[0..r].
+ *
  * Grid layout: x fastest, element (x, y, z) at x + nx*(y + ny*z); 2D uses
  * nz = 1 and dim = 2.  The sweep is a plain triple loop per time step over
  * a ping-pong buffer; OpenMP only splits the (z, y) rows across threads.
@@ -104,6 +116,54 @@ static void step_f32(const float *f, float *g, int64_t nx, int64_t ny, int64_t n
     }
 }
 
+static void step_shared_f64(const double *f, double *g, int64_t nx, int64_t ny, int64_t nz,
+                            int dim, int r, const double *c)
+{
+    int64_t rows = ny * nz;
+#pragma omp parallel for schedule(static)
+    for (int64_t row = 0; row < rows; ++row) {
+        int64_t y = row % ny, z = row / ny;
+        for (int64_t x = 0; x < nx; ++x) {
+            double acc = c[0] * f[IDX(x, y, z)];
+            for (int i = 1; i <= r; ++i) {
+                double sum = f[IDX(clamp_index(x - i, nx), y, z)] + f[IDX(clamp_index(x + i, nx), y, z)];
+                sum = sum + f[IDX(x, clamp_index(y - i, ny), z)];
+                sum = sum + f[IDX(x, clamp_index(y + i, ny), z)];
+                if (dim == 3) {
+                    sum = sum + f[IDX(x, y, clamp_index(z - i, nz))];
+                    sum = sum + f[IDX(x, y, clamp_index(z + i, nz))];
+                }
+                acc = acc + c[i] * sum;
+            }
+            g[IDX(x, y, z)] = acc;
+        }
+    }
+}
+
+static void step_shared_f32(const float *f, float *g, int64_t nx, int64_t ny, int64_t nz,
+                            int dim, int r, const float *c)
+{
+    int64_t rows = ny * nz;
+#pragma omp parallel for schedule(static)
+    for (int64_t row = 0; row < rows; ++row) {
+        int64_t y = row % ny, z = row / ny;
+        for (int64_t x = 0; x < nx; ++x) {
+            float acc = c[0] * f[IDX(x, y, z)];
+            for (int i = 1; i <= r; ++i) {
+                float sum = f[IDX(clamp_index(x - i, nx), y, z)] + f[IDX(clamp_index(x + i, nx), y, z)];
+                sum = sum + f[IDX(x, clamp_index(y - i, ny), z)];
+                sum = sum + f[IDX(x, clamp_index(y + i, ny), z)];
+                if (dim == 3) {
+                    sum = sum + f[IDX(x, y, clamp_index(z - i, nz))];
+                    sum = sum + f[IDX(x, y, clamp_index(z + i, nz))];
+                }
+                acc = fmaf(c[i], sum, acc);
+            }
+            g[IDX(x, y, z)] = acc;
+        }
+    }
+}
+
 static int check_args(int64_t nx, int64_t ny, int64_t nz, int dim, int r, int iters)
 {
     if (nx <= 0 || ny <= 0 || nz <= 0 || iters < 0) return -1;
@@ -156,6 +216,44 @@ int oracle_sweep_f32(const float *in, float *out, int64_t nx, int64_t ny, int64_
     for (int s = 0; s < iters; ++s) {
         float *dst = ((iters - 1 - s) % 2 == 0) ? out : tmp;
         step_f32(src, dst, nx, ny, nz, dim, r, c);
+        src = dst;
+    }
+    free(tmp);
+    return 0;
+}
+
+int oracle_sweep_shared_f64(const double *in, double *out, int64_t nx, int64_t ny, int64_t nz,
+                            int dim, int r, const double *c, int iters, int nthreads)
+{
+    if (check_args(nx, ny, nz, dim, r, iters)) return -1;
+    int64_t n = nx * ny * nz;
+    set_threads(nthreads);
+    if (iters == 0) { memcpy(out, in, (size_t)n * sizeof(double)); return 0; }
+    double *tmp = (double *)malloc((size_t)n * sizeof(double));
+    if (!tmp) return -2;
+    const double *src = in;
+    for (int s = 0; s < iters; ++s) {
+        double *dst = ((iters - 1 - s) % 2 == 0) ? out : tmp;
+        step_shared_f64(src, dst, nx, ny, nz, dim, r, c);
+        src = dst;
+    }
+    free(tmp);
+    return 0;
+}
+
+int oracle_sweep_shared_f32(const float *in, float *out, int64_t nx, int64_t ny, int64_t nz,
+                            int dim, int r, const float *c, int iters, int nthreads)
+{
+    if (check_args(nx, ny, nz, dim, r, iters)) return -1;
+    int64_t n = nx * ny * nz;
+    set_threads(nthreads);
+    if (iters == 0) { memcpy(out, in, (size_t)n * sizeof(float)); return 0; }
+    float *tmp = (float *)malloc((size_t)n * sizeof(float));
+    if (!tmp) return -2;
+    const float *src = in;
+    for (int s = 0; s < iters; ++s) {
+        float *dst = ((iters - 1 - s) % 2 == 0) ? out : tmp;
+        step_shared_f32(src, dst, nx, ny, nz, dim, r, c);
         src = dst;
     }
     free(tmp);

@@ -28,14 +28,14 @@ STENCIL_F32, STENCIL_BF16, STENCIL_F16 = 0, 1, 2
 KERNEL_AUTO, KERNEL_STREAM, KERNEL_NAIVE = 0, 1, 2
 
 # every symbol include/stencil.h declares
-EXPORTS = ("stencil_create", "stencil_destroy", "stencil_run", "stencil_run_ex", "stencil_run_host",
+EXPORTS = ("stencil_create", "stencil_create_shared", "stencil_destroy", "stencil_run", "stencil_run_ex", "stencil_run_host",
            "stencil_default_schedule", "stencil_max_t", "stencil_get_device_status",
            "stencil_set_fault_injection", "stencil_run_noalloc", "stencil_run_batched", "stencil_tune",
            "stencil_schedule_features", "stencil_model_create", "stencil_model_destroy",
            "stencil_model_train", "stencil_model_predict", "stencil_model_normalization",
            "stencil_model_params", "stencil_model_grad", "stencil_last_cuda_error", "stencil_strerror")
 
-NFEAT = 12
+NFEAT = 14
 TUNE_ANALYTIC, TUNE_EXHAUSTIVE, TUNE_MODEL = 0, 1, 2
 
 
@@ -64,7 +64,7 @@ class BatchItem(ctypes.Structure):
 
 class Timing(ctypes.Structure):
     """stencil_timing: one candidate schedule with its features and times."""
-    _fields_ = [("sched", Schedule), ("features", ctypes.c_float * 12), ("ns_per_cell", ctypes.c_float),
+    _fields_ = [("sched", Schedule), ("features", ctypes.c_float * NFEAT), ("ns_per_cell", ctypes.c_float),
                 ("analytic_ns_per_cell", ctypes.c_float), ("model_ns_per_cell", ctypes.c_float)]
 
 
@@ -131,13 +131,26 @@ def _check(rc: int, what: str) -> int:
 
 
 # ------------------------------------------------------------ C-named calls
-def stencil_create(dim: int, radius: int, coeffs) -> int:
+def _create(fn: str, dim: int, radius: int, coeffs, k: int) -> int:
     import numpy as np
-    c = np.ascontiguousarray(coeffs, dtype=np.float32)
+    c = np.ascontiguousarray(coeffs, dtype=np.float32).reshape(-1)
+    if c.size < max(k, 1):   # the library reads k floats
+        raise ValueError(f"{fn}: need {k} coefficients, got {c.size}")
     h = ctypes.c_void_p()
-    _check(_lib().stencil_create(ctypes.byref(h), dim, radius,
-                                 c.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "stencil_create")
+    _check(getattr(_lib(), fn)(ctypes.byref(h), dim, radius, c.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), fn)
     return h.value
+
+
+def stencil_create(dim: int, radius: int, coeffs) -> int:
+    """K = 2*dim*radius + 1 coefficients, one per (distance, direction)."""
+    ok = dim in (2, 3) and 1 <= radius <= 6
+    return _create("stencil_create", dim, radius, coeffs, 2 * dim * radius + 1 if ok else 0)
+
+
+def stencil_create_shared(dim: int, radius: int, coeffs) -> int:
+    """K = radius + 1 coefficients, one per distance."""
+    ok = dim in (2, 3) and 1 <= radius <= 6
+    return _create("stencil_create_shared", dim, radius, coeffs, radius + 1 if ok else 0)
 
 
 def stencil_destroy(h: int) -> int:
@@ -306,11 +319,12 @@ def _dims(x, dim):
 
 
 class Stencil:
-    """A star stencil (dim, radius, K coefficients) bound to a library handle."""
+    """A star stencil (dim, radius, K coefficients) bound to a library handle;
+    shared=True: one coefficient per distance (K = radius + 1)."""
 
-    def __init__(self, dim: int, radius: int, coeffs):
-        self.dim, self.radius = dim, radius
-        self.handle = stencil_create(dim, radius, coeffs)
+    def __init__(self, dim: int, radius: int, coeffs, shared: bool = False):
+        self.dim, self.radius, self.shared = dim, radius, shared
+        self.handle = (stencil_create_shared if shared else stencil_create)(dim, radius, coeffs)
 
     def close(self):
         if self.handle:

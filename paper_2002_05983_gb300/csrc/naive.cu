@@ -23,7 +23,9 @@ template <> __device__ __forceinline__ __nv_bfloat16 st1<__nv_bfloat16>(float v)
 }
 template <> __device__ __forceinline__ __half st1<__half>(float v) { return __float2half_rn(v); }
 
-template <int D, int R, typename S>
+// SH: one coefficient per distance; the 2*D neighbours at distance i are summed
+// left to right (W, E, S, N[, B, A]) and then enter one FMA.
+template <int D, int R, typename S, bool SH>
 __global__ void __launch_bounds__(256)
     naive_kernel(const S *__restrict__ in, S *__restrict__ out, const __grid_constant__ NaiveArgs a)
 {
@@ -41,6 +43,17 @@ __global__ void __launch_bounds__(256)
         float acc = __fmul_rn(a.c[0], at(x, y, z));
 #pragma unroll
         for (int i = 1; i <= R; ++i) {
+            if constexpr (SH) {
+                float sum = __fadd_rn(at(max(x - i, 0), y, z), at(min(x + i, a.nx - 1), y, z));
+                sum = __fadd_rn(sum, at(x, max(y - i, 0), z));
+                sum = __fadd_rn(sum, at(x, min(y + i, a.ny - 1), z));
+                if (D == 3) {
+                    sum = __fadd_rn(sum, at(x, y, max(z - i, 0)));
+                    sum = __fadd_rn(sum, at(x, y, min(z + i, a.nz - 1)));
+                }
+                acc = __fmaf_rn(a.c[i], sum, acc);
+                continue;
+            }
             const int cb = 1 + (i - 1) * 2 * D;
             acc = __fmaf_rn(a.c[cb + 0], at(max(x - i, 0), y, z), acc);
             acc = __fmaf_rn(a.c[cb + 1], at(min(x + i, a.nx - 1), y, z), acc);
@@ -55,38 +68,44 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-template <int D, int R>
-const void *pick(int dtype)
+template <int D, int R, bool SH>
+const void *pick_sh(int dtype)
 {
     switch (dtype) {
-    case 0: return reinterpret_cast<const void *>(&naive_kernel<D, R, float>);
-    case 1: return reinterpret_cast<const void *>(&naive_kernel<D, R, __nv_bfloat16>);
-    case 2: return reinterpret_cast<const void *>(&naive_kernel<D, R, __half>);
+    case 0: return reinterpret_cast<const void *>(&naive_kernel<D, R, float, SH>);
+    case 1: return reinterpret_cast<const void *>(&naive_kernel<D, R, __nv_bfloat16, SH>);
+    case 2: return reinterpret_cast<const void *>(&naive_kernel<D, R, __half, SH>);
     default: return nullptr;
     }
 }
 
+template <int D, int R>
+const void *pick(int dtype, int sh)
+{
+    return sh ? pick_sh<D, R, true>(dtype) : pick_sh<D, R, false>(dtype);
+}
+
 }  // namespace
 
-const void *naive_fn(int dim, int r, int dtype)
+const void *naive_fn(int dim, int r, int dtype, int sh)
 {
     if (dim == 2) {
         switch (r) {
-        case 1: return pick<2, 1>(dtype);
-        case 2: return pick<2, 2>(dtype);
-        case 3: return pick<2, 3>(dtype);
-        case 4: return pick<2, 4>(dtype);
-        case 5: return pick<2, 5>(dtype);
-        case 6: return pick<2, 6>(dtype);
+        case 1: return pick<2, 1>(dtype, sh);
+        case 2: return pick<2, 2>(dtype, sh);
+        case 3: return pick<2, 3>(dtype, sh);
+        case 4: return pick<2, 4>(dtype, sh);
+        case 5: return pick<2, 5>(dtype, sh);
+        case 6: return pick<2, 6>(dtype, sh);
         }
     } else if (dim == 3) {
         switch (r) {
-        case 1: return pick<3, 1>(dtype);
-        case 2: return pick<3, 2>(dtype);
-        case 3: return pick<3, 3>(dtype);
-        case 4: return pick<3, 4>(dtype);
-        case 5: return pick<3, 5>(dtype);
-        case 6: return pick<3, 6>(dtype);
+        case 1: return pick<3, 1>(dtype, sh);
+        case 2: return pick<3, 2>(dtype, sh);
+        case 3: return pick<3, 3>(dtype, sh);
+        case 4: return pick<3, 4>(dtype, sh);
+        case 5: return pick<3, 5>(dtype, sh);
+        case 6: return pick<3, 6>(dtype, sh);
         }
     }
     return nullptr;

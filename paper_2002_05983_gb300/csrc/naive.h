@@ -14,7 +14,8 @@ struct NaiveArgs {
     float c[kMaxK];
 };
 
-// __global__ naive_kernel<dim, r, S>(const S* in, S* out, NaiveArgs) for dtype 0/1/2, or nullptr.
-const void *naive_fn(int dim, int r, int dtype);
+// __global__ naive_kernel<dim, r, S, sh>(const S* in, S* out, NaiveArgs) for dtype 0/1/2, or
+// nullptr; sh = 1: one coefficient per distance.
+const void *naive_fn(int dim, int r, int dtype, int sh);
 
 }  // namespace stn

@@ -20,6 +20,7 @@
 
 struct stencil_plan {
     int dim = 0, r = 0, K = 0;
+    int shared = 0;              // 1: one coefficient per distance (K = r + 1)
     float c[stn::kMaxK] = {};
     void *scratch = nullptr;     // second grid of the ping-pong between passes
     size_t scratch_bytes = 0;
@@ -78,7 +79,8 @@ struct Registry {
                            stn::list_2d_f32_r5,  stn::list_2d_f32_r6,  stn::list_3d_f32_r5,
                            stn::list_3d_f32_r6,  stn::list_2d_bf16_r5, stn::list_2d_bf16_r6,
                            stn::list_3d_bf16_r5, stn::list_3d_bf16_r6, stn::list_2d_f16_r5,
-                           stn::list_2d_f16_r6,  stn::list_3d_f16_r5,  stn::list_3d_f16_r6};
+                           stn::list_2d_f16_r6,  stn::list_3d_f16_r5,  stn::list_3d_f16_r6,
+                           stn::list_2d_f32sh,   stn::list_3d_f32sh};
         for (L f : lists) {
             const stn::KernelEntry *e = nullptr;
             const int n = f(&e);
@@ -86,19 +88,19 @@ struct Registry {
         }
     }
     // tx / ty = 0: the default block shape (the first listed for that degree)
-    const stn::KernelEntry *find(int dim, int r, int t, int vy, int dtype, int tx = 0, int ty = 0) const
+    const stn::KernelEntry *find(int dim, int r, int t, int vy, int dtype, int sh, int tx = 0, int ty = 0) const
     {
         for (const auto &e : all)
             if (e.dim == dim && e.r == r && e.t == t && (dim == 2 || e.vy == vy) && e.dtype == dtype &&
-                (!tx || e.tx == tx) && (dim == 2 || !ty || e.ty == ty))
+                e.sh == sh && (!tx || e.tx == tx) && (dim == 2 || !ty || e.ty == ty))
                 return &e;
         return nullptr;
     }
-    int max_t(int dim, int r, int dtype, int vy) const
+    int max_t(int dim, int r, int dtype, int vy, int sh) const
     {
         int m = 0;
         for (const auto &e : all)
-            if (e.dim == dim && e.r == r && e.dtype == dtype && (dim == 2 || e.vy == vy))
+            if (e.dim == dim && e.r == r && e.dtype == dtype && (dim == 2 || e.vy == vy) && e.sh == sh)
                 m = std::max(m, e.t);
         return m;
     }
@@ -193,10 +195,12 @@ void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz,
     (void)nz;
     const Registry &reg = registry();
     stencil_schedule d{};
-    d.kernel = stream_applicable(dtype, nx) ? STENCIL_KERNEL_STREAM : STENCIL_KERNEL_NAIVE;
+    // shared-coefficient stencils have FP32 streaming kernels only; other storage runs naive
+    const bool have = reg.max_t(h->dim, h->r, dtype, h->dim == 3 ? 2 : 1, h->shared) > 0;
+    d.kernel = (have && stream_applicable(dtype, nx)) ? STENCIL_KERNEL_STREAM : STENCIL_KERNEL_NAIVE;
     if (h->dim == 2) {
         static const int t2[stn::kMaxR + 1] = {0, 5, 3, 2, 2, 2, 2};
-        d.t = std::min(t2[h->r], reg.max_t(2, h->r, dtype, 1));
+        d.t = std::max(1, std::min(t2[h->r], reg.max_t(2, h->r, dtype, 1, h->shared)));
         d.threads_x = 128;
         d.threads_y = 1;
         d.rows_per_thread = 1;
@@ -217,7 +221,7 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
 {
     const int D = h->dim, R = h->r;
     const int vy = D == 3 ? s.rows_per_thread : 1;
-    const stn::KernelEntry *e = registry().find(D, R, t, vy, dtype, s.threads_x, D == 3 ? s.threads_y : 0);
+    const stn::KernelEntry *e = registry().find(D, R, t, vy, dtype, h->shared, s.threads_x, D == 3 ? s.threads_y : 0);
     if (!e) return STENCIL_ERR_UNSUPPORTED;
     if (s.prefetch && s.prefetch != e->pf) return STENCIL_ERR_UNSUPPORTED;
     if (e->smem > static_cast<size_t>(dev.max_smem)) return STENCIL_ERR_UNSUPPORTED;
@@ -361,7 +365,7 @@ int check_problem(const stencil_plan *h, const void *in, const void *out, int64_
 int launch_naive(const stencil_plan *h, const void *src, void *dst, int64_t nx, int64_t ny,
                  int64_t nz, int dtype, cudaStream_t st, const DevInfo &dev)
 {
-    const void *fn = stn::naive_fn(h->dim, h->r, dtype);
+    const void *fn = stn::naive_fn(h->dim, h->r, dtype, h->shared);
     if (!fn) return STENCIL_ERR_UNSUPPORTED;
     stn::NaiveArgs na{};
     na.nx = static_cast<int>(nx);
@@ -476,7 +480,7 @@ int resolve(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype
     out.threads_x = static_cast<int>(ps.block.x);
     out.threads_y = static_cast<int>(ps.block.y);
     out.seg = ps.a.seg;
-    const stn::KernelEntry *e = registry().find(h->dim, h->r, s.t, h->dim == 3 ? s.rows_per_thread : 1, dtype,
+    const stn::KernelEntry *e = registry().find(h->dim, h->r, s.t, h->dim == 3 ? s.rows_per_thread : 1, dtype, h->shared,
                                                 out.threads_x, out.threads_y);
     out.prefetch = e ? e->pf : 0;
     if (h->dim == 2) out.rows_per_thread = 1;
@@ -488,7 +492,7 @@ double analytic_ns(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, in
                    int occ)
 {
     const int D = h->dim, R = h->r, t = s.t;
-    const stn::KernelEntry *e = registry().find(D, R, t, D == 3 ? s.rows_per_thread : 1, dtype, s.threads_x,
+    const stn::KernelEntry *e = registry().find(D, R, t, D == 3 ? s.rows_per_thread : 1, dtype, h->shared, s.threads_x,
                                                 s.threads_y);
     if (!e) return 1e9;
     const double es = elem_bytes(dtype);
@@ -510,8 +514,9 @@ double analytic_ns(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, in
 }
 
 void features_of(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, const stencil_schedule &s,
-                 int occ, double analytic, float *f)
+                 const Pass &ps, double analytic, float *f)
 {
+    const int occ = ps.occ;
     f[0] = static_cast<float>(h->dim);
     f[1] = static_cast<float>(h->r);
     f[2] = static_cast<float>(std::log2(static_cast<double>(nx)));
@@ -526,6 +531,9 @@ void features_of(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int 
     f[9] = static_cast<float>(std::log2(static_cast<double>(2 * h->r + 1) * s.t * 4 * vy * (2 * h->dim * h->r + 1)));
     f[10] = static_cast<float>(std::log2(static_cast<double>(s.seg)));
     f[11] = static_cast<float>(std::log2(analytic));
+    // work partition: block order (strips end to end or slabs) and waves of resident blocks
+    f[12] = static_cast<float>(ps.a.flat);
+    f[13] = static_cast<float>(std::log2(static_cast<double>(ps.grid.x) / (152.0 * std::max(occ, 1))));
 }
 
 // Candidate schedules (unresolved) of a problem.
@@ -538,7 +546,7 @@ int candidates(const stencil_plan *h, int64_t ny, int64_t nz, int dtype, stencil
     const int *segs = h->dim == 2 ? segs2 : segs3;
     for (int vy : {2, 4}) {
         if (h->dim == 2 && vy == 4) break;
-        const int tmax = registry().max_t(h->dim, h->r, dtype, h->dim == 3 ? vy : 1);
+        const int tmax = registry().max_t(h->dim, h->r, dtype, h->dim == 3 ? vy : 1, h->shared);
         for (int t = 1; t <= tmax; ++t)
             for (int k = 0; k < 5; ++k) {
                 if (segs[k] > ns) continue;
@@ -627,7 +635,7 @@ int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cuda
         // largest compiled degree <= the chosen one that divides iters
         int t = std::max(1, std::min(s.t, b.iters));
         while (t > 1 && (b.iters % t != 0 || !registry().find(h->dim, h->r, t, h->dim == 3 ? s.rows_per_thread : 1,
-                                                                b.dtype, s.threads_x, s.threads_y)))
+                                                                b.dtype, h->shared, s.threads_x, s.threads_y)))
             --t;
         s.t = t;
         Item x;
@@ -637,7 +645,7 @@ int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cuda
         x.rows = h->dim == 3 ? s.rows_per_thread : 1;
         int rc = plan_pass(h, b.nx, b.ny, b.nz, b.dtype, t, s, dev, x.ps, true);
         if (rc) return rc;
-        x.e = registry().find(h->dim, h->r, t, x.rows, b.dtype, s.threads_x, s.threads_y);
+        x.e = registry().find(h->dim, h->r, t, x.rows, b.dtype, h->shared, s.threads_x, s.threads_y);
         if (!x.e) return STENCIL_ERR_UNSUPPORTED;
         x.ps.a.timeout_ms = h->timeout_ms;
         it.push_back(x);
@@ -813,6 +821,22 @@ int stencil_create(stencil_handle *out, int dim, int radius, const float *coeffs
     return STENCIL_OK;
 }
 
+int stencil_create_shared(stencil_handle *out, int dim, int radius, const float *coeffs)
+{
+    if (!out || !coeffs) return STENCIL_ERR_INVALID_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || radius < 1 || radius > stn::kMaxR) return STENCIL_ERR_INVALID_ARG;
+    stencil_plan *h = new (std::nothrow) stencil_plan;
+    if (!h) return STENCIL_ERR_OOM;
+    h->dim = dim;
+    h->r = radius;
+    h->shared = 1;
+    h->K = radius + 1;
+    std::memcpy(h->c, coeffs, sizeof(float) * h->K);
+    *out = h;
+    return STENCIL_OK;
+}
+
 int stencil_destroy(stencil_handle h)
 {
     if (!h) return STENCIL_OK;
@@ -878,7 +902,7 @@ int stencil_default_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t n
 
 int stencil_max_t(int dim, int radius, int dtype, int rows_per_thread)
 {
-    return registry().max_t(dim, radius, dtype, rows_per_thread);
+    return registry().max_t(dim, radius, dtype, rows_per_thread, 0);
 }
 
 int stencil_get_device_status(void *stream, int clear)
@@ -1049,7 +1073,7 @@ int stencil_schedule_features(stencil_handle h, int64_t nx, int64_t ny, int64_t 
     Pass ps;
     rc = resolve(h, nx, ny, nz, dtype, s, *dev, r, ps);
     if (rc) return rc;
-    features_of(h, nx, ny, nz, dtype, r, ps.occ, analytic_ns(h, nx, ny, nz, dtype, r, ps.occ), features);
+    features_of(h, nx, ny, nz, dtype, r, ps, analytic_ns(h, nx, ny, nz, dtype, r, ps.occ), features);
     return STENCIL_OK;
 }
 
@@ -1080,7 +1104,7 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
         stencil_timing tm{};
         tm.sched = r;
         tm.analytic_ns_per_cell = static_cast<float>(analytic_ns(h, nx, ny, nz, dtype, r, ps.occ));
-        features_of(h, nx, ny, nz, dtype, r, ps.occ, tm.analytic_ns_per_cell, tm.features);
+        features_of(h, nx, ny, nz, dtype, r, ps, tm.analytic_ns_per_cell, tm.features);
         tm.ns_per_cell = -1.f;
         tm.model_ns_per_cell = -1.f;
         tim.push_back(tm);

@@ -420,7 +420,7 @@ __device__ __forceinline__ void mbar_inval(uint32_t bar)
 // one thread block.  Returns false if a bounded wait expired (the device
 // status word is then set).  Leaves the block's shared memory free for the
 // next piece.
-template <int D, int R, int T, int VY, typename S, int TX, int TY>
+template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH>
 __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepArgs &a, int col, int Z0, int Z1,
                                            unsigned char *smem)
 {
@@ -454,7 +454,8 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     // are uniform), so each FMA reads them from the register file instead of uniform
     // registers refilled from the constant bank inside the loop (measured 2-8 % faster
     // for r >= 2; 3D kernels, tighter on registers, gain nothing and keep the default).
-    constexpr int K = 1 + 2 * D * R;
+    // SH: one coefficient per distance, c[0] centre and c[i] for distance i.
+    constexpr int K = SH ? 1 + R : 1 + 2 * D * R;
     float cf[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
@@ -702,23 +703,39 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                 float acc = __fmul_rn(cf[0], ctr[vy][v]);
 #pragma unroll
                 for (int i = 1; i <= R; ++i) {
-                    const int cb = 1 + (i - 1) * K2;
+                    const int cb = SH ? i : 1 + (i - 1) * K2;
                     const float w = (v - i >= 0) ? ctr[vy][cclamp(v - i, 0, 3)]
                                                  : L[cclamp((i - v - 1) / 4, 0, NV - 1)][cclamp(v - i + 4 * ((i - v - 1) / 4 + 1), 0, 3)];
                     const float e = (v + i <= 3) ? ctr[vy][cclamp(v + i, 0, 3)]
                                                  : Rr[cclamp((v + i) / 4 - 1, 0, NV - 1)][cclamp((v + i) % 4, 0, 3)];
-                    acc = __fmaf_rn(cf[cb + 0], w, acc);
-                    acc = __fmaf_rn(cf[cb + 1], e, acc);
+                    float sv = 0.f, nv = 0.f;
                     if constexpr (D == 3) {
-                        const float sv = (vy - i >= 0) ? ctr[cclamp(vy - i, 0, VY - 1)][v]
-                                                       : up[cclamp(i - vy - 1, 0, R - 1)][v];
-                        const float nv = (vy + i < VY) ? ctr[cclamp(vy + i, 0, VY - 1)][v]
-                                                       : dn[cclamp(vy + i - VY, 0, R - 1)][v];
-                        acc = __fmaf_rn(cf[cb + 2], sv, acc);
-                        acc = __fmaf_rn(cf[cb + 3], nv, acc);
+                        sv = (vy - i >= 0) ? ctr[cclamp(vy - i, 0, VY - 1)][v] : up[cclamp(i - vy - 1, 0, R - 1)][v];
+                        nv = (vy + i < VY) ? ctr[cclamp(vy + i, 0, VY - 1)][v] : dn[cclamp(vy + i - VY, 0, R - 1)][v];
                     }
-                    acc = __fmaf_rn(cf[cb + K2 - 2], q[s - 1][qrd(s, J, -i)][vy][v], acc);
-                    acc = __fmaf_rn(cf[cb + K2 - 1], q[s - 1][qrd(s, J, i)][vy][v], acc);
+                    const float bz = q[s - 1][qrd(s, J, -i)][vy][v];   // stream axis: S (2D) / B (3D)
+                    const float az = q[s - 1][qrd(s, J, i)][vy][v];    // N (2D) / A (3D)
+                    if constexpr (SH) {
+                        // neighbours at distance i summed left to right (W, E, S, N[, B, A]),
+                        // then one FMA with the shared coefficient
+                        float sum = __fadd_rn(w, e);
+                        if constexpr (D == 3) {
+                            sum = __fadd_rn(sum, sv);
+                            sum = __fadd_rn(sum, nv);
+                        }
+                        sum = __fadd_rn(sum, bz);
+                        sum = __fadd_rn(sum, az);
+                        acc = __fmaf_rn(cf[cb], sum, acc);
+                    } else {
+                        acc = __fmaf_rn(cf[cb + 0], w, acc);
+                        acc = __fmaf_rn(cf[cb + 1], e, acc);
+                        if constexpr (D == 3) {
+                            acc = __fmaf_rn(cf[cb + 2], sv, acc);
+                            acc = __fmaf_rn(cf[cb + 3], nv, acc);
+                        }
+                        acc = __fmaf_rn(cf[cb + K2 - 2], bz, acc);
+                        acc = __fmaf_rn(cf[cb + K2 - 1], az, acc);
+                    }
                 }
                 res[vy][v] = acc;
             }
@@ -891,7 +908,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
 // column b mod (ntx*nty), planes [j*seg, (j+1)*seg) with j = b / (ntx*nty),
 // so blocks running together cover neighbouring tiles of the same planes and
 // share their overlapping halo reads in L2.
-template <int D, int R, int T, int VY, typename S, int TX, int TY>
+template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH>
 __device__ __forceinline__ bool sweep_block(const CUtensorMap *tmap, const SweepArgs &a, int b, unsigned char *smem)
 {
     const int cols = a.ntx * a.nty;
@@ -910,7 +927,7 @@ __device__ __forceinline__ bool sweep_block(const CUtensorMap *tmap, const Sweep
         const int col = static_cast<int>(w / a.ns);
         const int z0 = static_cast<int>(w - static_cast<int64_t>(col) * a.ns);
         const int z1 = static_cast<int>(min(static_cast<int64_t>(a.ns), z0 + (we - w)));
-        ok = sweep_tile<D, R, T, VY, S, TX, TY>(tmap, a, col, z0, z1, smem);
+        ok = sweep_tile<D, R, T, VY, S, TX, TY, SH>(tmap, a, col, z0, z1, smem);
         w += z1 - z0;
     }
     return ok;
@@ -918,12 +935,12 @@ __device__ __forceinline__ bool sweep_block(const CUtensorMap *tmap, const Sweep
 
 // ------------------------------------------------------------------ kernels
 // One pass over the grid: block b sweeps its planes of the tile columns (sweep_block).
-template <int D, int R, int T, int VY, typename S, int TX, int TY>
+template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH>
 __global__ void __launch_bounds__(TX *TY)
     sweep_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ SweepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    sweep_block<D, R, T, VY, S, TX, TY>(&tmap, a, static_cast<int>(blockIdx.x), smem);
+    sweep_block<D, R, T, VY, S, TX, TY, SH>(&tmap, a, static_cast<int>(blockIdx.x), smem);
 }
 
 // Persistent sweep of many grids of one kernel class, all passes, from a device tile
@@ -961,7 +978,7 @@ __device__ __forceinline__ void fence_proxy_async_global()
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-template <int D, int R, int T, int VY, typename S, int TX, int TY>
+template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH>
 __global__ void __launch_bounds__(TX *TY)
     sweep_persistent(const __grid_constant__ BatchArgs B)
 {
@@ -1007,7 +1024,7 @@ __global__ void __launch_bounds__(TX *TY)
         __syncthreads();
         if (!s_ok) break;
         const SweepArgs a = B.args[task];
-        const bool done = sweep_block<D, R, T, VY, S, TX, TY>(D == 3 ? B.maps + task : nullptr, a, q - tk.first, smem);
+        const bool done = sweep_block<D, R, T, VY, S, TX, TY, SH>(D == 3 ? B.maps + task : nullptr, a, q - tk.first, smem);
         __syncthreads();
         if (tid == 0 && task != B.fault_task) {
             __threadfence();

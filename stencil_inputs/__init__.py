@@ -17,6 +17,8 @@ lists in Section IV.C; these stand in for them):
   * grid values: uniform [0, 1) from seed 0, x fastest;
   * coefficients: K = 2*D*r + 1 weights u_k + 2**-25 from seed 1, divided by
     their sum in fp64 and rounded to fp32 (nonnegative, sum ~1, distinct);
+    the one-per-distance form draws r + 1 weights the same way and divides by
+    w_0 + 2*D*(w_1 + ... + w_r) (operator row sum ~1);
   * 3D workloads add a Gaussian bump exp(-|p - c|^2 / (2 sigma^2)),
     sigma = 16 cells, c = (nx//2, ny//2, nz//2), amplitude 1, summed in fp64
     and rounded once to fp32.
@@ -77,6 +79,13 @@ def coefficients(dim: int, radius: int, seed: int = COEFF_SEED) -> np.ndarray:
     if len(np.unique(c)) != k:
         raise ValueError("coefficient draw is not distinct; choose another seed")
     return c
+
+
+def shared_coefficients(dim: int, radius: int, seed: int = COEFF_SEED) -> np.ndarray:
+    """Nonnegative fp32 coefficients of the one-per-distance form: c[0] the centre,
+    c[i] every neighbour at distance i; normalised so that c[0] + 2*dim*sum(c[1:]) ~ 1."""
+    w = uniform(seed, radius + 1).astype(np.float64) + 2.0 ** -25
+    return (w / (w[0] + 2 * dim * w[1:].sum())).astype(np.float32)
 
 
 def grid_shape(dim: int, nx: int, ny: int, nz: int = 1) -> tuple:

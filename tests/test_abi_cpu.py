@@ -47,6 +47,15 @@ def test_create_validates_on_host(lib):
         assert e.value.code == st.STENCIL_ERR_INVALID_ARG
     h = st.stencil_create(2, 1, c)
     assert st.stencil_destroy(h) == 0
+    # one coefficient per distance: K = r + 1
+    for dim, r in ((1, 1), (2, 0), (3, 7)):
+        with pytest.raises(st.StencilError) as e:
+            st.stencil_create_shared(dim, r, c)
+        assert e.value.code == st.STENCIL_ERR_INVALID_ARG
+    h = st.stencil_create_shared(3, 4, c)
+    assert st.stencil_destroy(h) == 0
+    with pytest.raises(ValueError):   # fewer coefficients than the library would read
+        st.stencil_create(2, 4, c)
 
 
 def test_run_rejects_bad_problems_before_touching_cuda(lib):

@@ -307,3 +307,77 @@ def test_rejects_bad_arguments(oracle_mod):
         oracle_mod.sweep_f32(np.zeros((3, 3), np.float32), 2, 1, np.zeros(4), 1)
     with pytest.raises(ValueError):
         oracle_mod.sweep_f64(np.zeros((3, 3, 3)), 2, 1, np.zeros(5), 1)
+
+
+# ---------------------------------------------------------------- shared-coefficient form
+def expand_shared(dim, r, cs):
+    """Per-(distance, direction) coefficients of a shared-coefficient stencil: c_{i,d} = c_i."""
+    c = np.zeros(2 * dim * r + 1, dtype=np.float64)
+    c[0] = cs[0]
+    for i in range(1, r + 1):
+        c[1 + (i - 1) * 2 * dim:1 + i * 2 * dim] = cs[i]
+    return c
+
+
+def shared_coeffs(dim, r):
+    return gen.shared_coefficients(dim, r, seed=4)
+
+
+@pytest.mark.parametrize("dim,nx,ny,nz,r", [(2, 6, 7, 1, 1), (2, 5, 9, 1, 3), (3, 4, 3, 5, 2), (3, 3, 4, 2, 4)])
+def test_shared_form_is_the_dense_operator_with_equal_coefficients(oracle_mod, dim, nx, ny, nz, r):
+    """Sharing one coefficient per distance is Eq. 1 with c_{i,d} = c_i: the FP64 shared
+    oracle equals the dense operator built from the expanded coefficients."""
+    cs = shared_coeffs(dim, r).astype(np.float64)
+    rng = np.random.default_rng(40 + r)
+    f = rng.random(shape_of(dim, nx, ny, nz))
+    a = dense_operator(dim, r, expand_shared(dim, r, cs), nx, ny, nz)
+    ref = (np.linalg.matrix_power(a, 3) @ f.reshape(-1)).reshape(f.shape)
+    np.testing.assert_allclose(oracle_mod.sweep_shared_f64(f, dim, r, cs, 3), ref, rtol=1e-13, atol=1e-15)
+
+
+def exact_shared_fp32_sweep(f, dim, r, cs, iters):
+    """Brute force of the FP32 shared form with exact rationals: every add of the left-to-right
+    neighbour sum rounded once, then one FMA (exact product + sum, rounded once) per distance."""
+    cq = [Fraction(float(v)) for v in cs]
+    cur = np.vectorize(lambda v: Fraction(float(v)), otypes=[object])(f)
+    shp = cur.shape
+    for _ in range(iters):
+        nxt = np.empty(shp, dtype=object)
+        for idx in np.ndindex(*shp):
+            pos = list(idx[::-1])
+            acc = rne_f32(cq[0] * cur[idx])
+            for i in range(1, r + 1):
+                vals = []
+                for e in DIRS[dim]:
+                    q = [min(max(pos[a] + i * e[a], 0), shp[::-1][a] - 1) for a in range(dim)]
+                    vals.append(cur[tuple(q[::-1])])
+                s = vals[0]
+                for v in vals[1:]:
+                    s = rne_f32(s + v)
+                acc = rne_f32(cq[i] * s + acc)
+            nxt[idx] = acc
+        cur = nxt
+    return np.vectorize(float, otypes=[np.float64])(cur)
+
+
+@pytest.mark.parametrize("dim,nx,ny,nz,r,iters", [(2, 6, 5, 1, 2, 2), (2, 4, 3, 1, 4, 1), (3, 3, 4, 3, 1, 2),
+                                                  (3, 2, 3, 2, 3, 1)])
+def test_shared_fp32_exact_rational_bruteforce(oracle_mod, dim, nx, ny, nz, r, iters):
+    cs = shared_coeffs(dim, r)
+    f = gen.uniform_grid(shape_of(dim, nx, ny, nz), seed=12)
+    ref = exact_shared_fp32_sweep(f, dim, r, cs, iters).astype(np.float32)
+    assert np.array_equal(oracle_mod.sweep_shared_f32(f, dim, r, cs, iters), ref)
+
+
+def test_shared_fp32_differs_from_full_chain_but_agrees_with_fp64():
+    """The shared FP32 order is its own rounding sequence (not the full form's FMA chain
+    with equal coefficients), and within 2e-6 * iters of FP64."""
+    import oracle
+    dim, r, iters = 2, 4, 10
+    cs = shared_coeffs(dim, r)
+    f = gen.uniform_grid((40, 48), seed=13)
+    got = oracle.sweep_shared_f32(f, dim, r, cs, iters)
+    full = oracle.sweep_f32(f, dim, r, expand_shared(dim, r, cs).astype(np.float32), iters)
+    assert not np.array_equal(got, full)
+    w64 = oracle.sweep_shared_f64(f.astype(np.float64), dim, r, cs.astype(np.float64), iters)
+    assert np.max(np.abs(got - w64)) <= 2e-6 * iters
