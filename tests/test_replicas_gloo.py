@@ -71,3 +71,20 @@ def test_reference_arm_runs_on_rank_zero_only():
                          capture_output=True, text=True, timeout=120)
     assert out.returncode == 0
     assert out.stdout.strip() == ""
+
+
+def test_gpu_local_cpus_from_topology(monkeypatch):
+    """CPU affinity column of nvidia-smi's topology matrix, intersected with the allowed CPUs."""
+    topo = ("\tGPU0\tGPU1\tNIC0\tCPU Affinity\tNUMA Affinity\tGPU NUMA ID\n"
+            "GPU0\t X \tNV18\tSYS\t0-3,8\t0\t2\n"
+            "GPU1\tNV18\t X \tSYS\t4-7\t1\t3\n")
+
+    class Out:
+        stdout = topo
+
+    monkeypatch.setattr(bench.subprocess, "run", lambda *a, **k: Out())
+    monkeypatch.setattr(bench.os, "sched_getaffinity", lambda pid: set(range(6)))
+    assert bench.gpu_local_cpus(0) == {0, 1, 2, 3}
+    assert bench.gpu_local_cpus(1) == {4, 5}
+    assert bench.gpu_local_cpus(2) is None
+    assert bench.parse_cpulist("0-2,5") == {0, 1, 2, 5} and bench.parse_cpulist("N/A") is None
