@@ -147,7 +147,7 @@ def gpu_local_cpus(index: int):
         return None
     lines = [ln for ln in out.splitlines() if ln.strip()]
     head = next((ln for ln in lines if "CPU Affinity" in ln), None)
-    row = next((ln for ln in lines if ln.split() and ln.split()[0] == f"GPU{index}"), None)
+    row = next((ln for ln in lines if ln is not head and ln.split() and ln.split()[0] == f"GPU{index}"), None)
     if not head or not row:
         return None
     cols = [c.strip() for c in head.split("\t")]
