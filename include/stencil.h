@@ -162,7 +162,9 @@ int stencil_run_host(stencil_handle h, const void *in_host, void *out_host, int6
                      int64_t ny, int64_t nz, int iters, int dtype, void *stream,
                      const stencil_schedule *sched);
 
-/* The schedule stencil_run would use for this problem (auto choice). */
+/* The schedule stencil_run would use for this problem when given none: the
+ * library's rule, overridden by a pick stored in the tuning-cache file (see
+ * stencil_tune), overridden by a pick stored on the handle. */
 int stencil_default_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
                              stencil_schedule *out);
 
@@ -181,8 +183,12 @@ int stencil_default_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t n
  * `chosen` receives the pick; `rows` (capacity `cap`, may be NULL) receives one
  * stencil_timing per candidate and *nrows their number.  With `store` != 0 the
  * pick is kept in the handle and used by later stencil_run calls on the same
- * (nx, ny, nz, dtype).  Errors: INVALID_ARG, UNSUPPORTED (no streaming kernel
- * for this shape), OOM, CUDA. */
+ * (nx, ny, nz, dtype); if the environment variable STENCIL_TUNE_CACHE names a
+ * file, the pick is also appended to it as one text line keyed by the GPU's
+ * name, dim, radius, coefficient form, dtype and (nx, ny, nz), and every handle
+ * in any process with the same setting uses it (the handle's own pick first).
+ * Errors: INVALID_ARG, UNSUPPORTED (no streaming kernel for this shape), OOM,
+ * CUDA. */
 int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype, int mode,
                  stencil_model_handle model, int store, stencil_schedule *chosen,
                  stencil_timing *rows, int cap, int *nrows);

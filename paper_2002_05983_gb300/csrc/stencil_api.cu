@@ -7,8 +7,11 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <mutex>
 #include <new>
+#include <sstream>
+#include <string>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -215,6 +218,109 @@ void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz,
     *s = d;
 }
 
+// ---- persistent tuning cache: the file named by STENCIL_TUNE_CACHE holds one line per
+// stored pick, "v1 <gpu> <dim> <r> <shared> <dtype> <nx> <ny> <nz> <kernel> <t> <threads_x>
+// <threads_y> <rows> <seg> <prefetch>", the last line for a key winning.  A pick is keyed by
+// the GPU's name and the problem (not the coefficients, which do not change the speed).
+struct FileCacheEntry {
+    std::string gpu;
+    int dim, r, sh, dtype;
+    int64_t nx, ny, nz;
+    stencil_schedule s;
+};
+std::mutex g_fc_mu;
+std::string g_fc_path;
+std::vector<FileCacheEntry> g_fc;
+
+bool gpu_name(std::string *out)
+{
+    static std::mutex mu;
+    static std::string names[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return false;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (names[dev].empty()) {
+        cudaDeviceProp p;
+        if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        std::string n = p.name;
+        for (char &c : n)
+            if (c == ' ' || c == '\t') c = '_';
+        names[dev] = n;
+    }
+    *out = names[dev];
+    return true;
+}
+
+// (Re)load the cache when STENCIL_TUNE_CACHE names another file; caller holds g_fc_mu.
+const char *fc_sync()
+{
+    const char *path = std::getenv("STENCIL_TUNE_CACHE");
+    if (!path || !*path) return nullptr;
+    if (g_fc_path != path) {
+        g_fc.clear();
+        g_fc_path = path;
+        std::ifstream f(path);
+        std::string line;
+        while (std::getline(f, line)) {
+            std::istringstream is(line);
+            std::string v;
+            FileCacheEntry e{};
+            if (!(is >> v >> e.gpu >> e.dim >> e.r >> e.sh >> e.dtype >> e.nx >> e.ny >> e.nz >> e.s.kernel >> e.s.t >>
+                  e.s.threads_x >> e.s.threads_y >> e.s.rows_per_thread >> e.s.seg >> e.s.prefetch) ||
+                v != "v1")
+                continue;   // not a cache line
+            g_fc.push_back(e);
+        }
+    }
+    return path;
+}
+
+bool fc_lookup(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, stencil_schedule *out)
+{
+    std::string gpu;
+    if (!std::getenv("STENCIL_TUNE_CACHE") || !gpu_name(&gpu)) return false;
+    std::lock_guard<std::mutex> lk(g_fc_mu);
+    if (!fc_sync()) return false;
+    bool hit = false;
+    for (const auto &e : g_fc)
+        if (e.gpu == gpu && e.dim == h->dim && e.r == h->r && e.sh == h->shared && e.dtype == dtype && e.nx == nx &&
+            e.ny == ny && e.nz == nz) {
+            *out = e.s;
+            hit = true;
+        }
+    return hit;
+}
+
+void fc_store(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, const stencil_schedule &s)
+{
+    std::string gpu;
+    if (!std::getenv("STENCIL_TUNE_CACHE") || !gpu_name(&gpu)) return;
+    std::lock_guard<std::mutex> lk(g_fc_mu);
+    const char *path = fc_sync();
+    if (!path) return;
+    std::ofstream f(path, std::ios::app);
+    f << "v1 " << gpu << ' ' << h->dim << ' ' << h->r << ' ' << h->shared << ' ' << dtype << ' ' << nx << ' ' << ny
+      << ' ' << nz << ' ' << s.kernel << ' ' << s.t << ' ' << s.threads_x << ' ' << s.threads_y << ' '
+      << s.rows_per_thread << ' ' << s.seg << ' ' << s.prefetch << '\n';
+    g_fc.push_back({gpu, h->dim, h->r, h->shared, dtype, nx, ny, nz, s});
+}
+
+// The schedule stencil_run uses when the caller gives none: the default rule, overridden
+// by a pick stored in the tuning-cache file, overridden by one stored on the handle.
+void chosen_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, stencil_schedule *s)
+{
+    default_schedule(h, nx, ny, nz, dtype, s);
+    fc_lookup(h, nx, ny, nz, dtype, s);
+    for (const auto &tu : h->tuned)
+        if (tu.nx == nx && tu.ny == ny && tu.nz == nz && tu.dtype == dtype) *s = tu.s;
+}
+
 // Fill one pass of temporal degree t.  Pointers are set by the caller.
 int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, int t,
               const stencil_schedule &s, const DevInfo &dev, Pass &ps, bool batched = false)
@@ -394,9 +500,7 @@ int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny,
         return 0;
     }
     stencil_schedule s;
-    default_schedule(h, nx, ny, nz, dtype, &s);
-    for (const auto &tu : h->tuned)
-        if (tu.nx == nx && tu.ny == ny && tu.nz == nz && tu.dtype == dtype) s = tu.s;
+    chosen_schedule(h, nx, ny, nz, dtype, &s);
     if (user) {
         if (user->kernel < 0 || user->kernel > STENCIL_KERNEL_NAIVE) return STENCIL_ERR_INVALID_ARG;
         if (user->kernel) s.kernel = user->kernel;
@@ -607,10 +711,10 @@ std::vector<char> batch_key(const stencil_batch_item *items, int n, int dev)
         k.insert(k.end(), c, c + sizeof(float) * h->K);
         int extra[2] = {h->fault_plane, h->timeout_ms};
         k.insert(k.end(), reinterpret_cast<char *>(extra), reinterpret_cast<char *>(extra) + sizeof(extra));
-        for (const auto &tu : h->tuned) {
-            const char *b = reinterpret_cast<const char *>(&tu);
-            k.insert(k.end(), b, b + sizeof(tu));
-        }
+        stencil_schedule sc;   // the schedule the batch will use for this grid
+        chosen_schedule(h, items[i].nx, items[i].ny, items[i].nz, items[i].dtype, &sc);
+        const char *b = reinterpret_cast<const char *>(&sc);
+        k.insert(k.end(), b, b + sizeof(sc));
     }
     return k;
 }
@@ -628,9 +732,7 @@ int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cuda
         const stencil_batch_item &b = items[i];
         stencil_plan *h = b.h;
         stencil_schedule s;
-        default_schedule(h, b.nx, b.ny, b.nz, b.dtype, &s);
-        for (const auto &tu : h->tuned)
-            if (tu.nx == b.nx && tu.ny == b.ny && tu.nz == b.nz && tu.dtype == b.dtype) s = tu.s;
+        chosen_schedule(h, b.nx, b.ny, b.nz, b.dtype, &s);
         if (s.kernel != STENCIL_KERNEL_STREAM) return STENCIL_ERR_UNSUPPORTED;
         // largest compiled degree <= the chosen one that divides iters
         int t = std::max(1, std::min(s.t, b.iters));
@@ -896,7 +998,7 @@ int stencil_default_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t n
                              stencil_schedule *out)
 {
     if (!h || !out || dtype < STENCIL_F32 || dtype > STENCIL_F16) return STENCIL_ERR_INVALID_ARG;
-    default_schedule(h, nx, ny, nz, dtype, out);
+    chosen_schedule(h, nx, ny, nz, dtype, out);
     return STENCIL_OK;
 }
 
@@ -1170,6 +1272,7 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
                 found = true;
             }
         if (!found) h->tuned.push_back({nx, ny, nz, dtype, *chosen});
+        fc_store(h, nx, ny, nz, dtype, *chosen);
     }
     if (rows)
         for (int i = 0; i < nc && i < cap; ++i) rows[i] = tim[i];

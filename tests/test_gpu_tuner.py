@@ -130,3 +130,28 @@ def test_tuning_problem_set_is_streamable():
     for p in tune.tuning_problems(20):
         assert p["nx"] % 8 == 0 and p["nx"] >= 64
         assert 1 <= p["r"] <= 4 and p["dim"] in (2, 3)
+
+
+def test_tuning_cache_file_is_shared_between_handles(tmp_path, monkeypatch):
+    """A pick stored with STENCIL_TUNE_CACHE set is appended to that file and becomes the
+    schedule of a fresh handle of the same problem; a bit-exact run follows it."""
+    path = tmp_path / "tune.cache"
+    monkeypatch.setenv("STENCIL_TUNE_CACHE", str(path))
+    dim, r, nx, ny = 2, 3, 1024, 520
+    c = gen.coefficients(dim, r)
+    a = st.Stencil(dim, r, c)
+    base = a.default_schedule((ny, nx))
+    chosen, _ = st.stencil_tune(a.handle, nx, ny, 1, st.STENCIL_F32, st.TUNE_ANALYTIC, store=True)
+    line = path.read_text().strip().splitlines()[-1].split()
+    assert line[0] == "v1" and [int(v) for v in line[2:9]] == [dim, r, 0, 0, nx, ny, 1]
+    b = st.Stencil(dim, r, c)
+    got = b.default_schedule((ny, nx))
+    assert (got.t, got.seg, got.kernel) == (chosen.t, chosen.seg, chosen.kernel)
+    f = gen.workload_grid(dim, nx, ny)
+    out = b.run(torch.from_numpy(f).cuda(), 7).cpu().numpy()
+    assert np.array_equal(out, oracle.sweep_f32(f, dim, r, c, 7))
+    # another shape is not affected; without the variable the file is ignored
+    assert b.default_schedule((ny, nx + 8)).t == base.t
+    monkeypatch.delenv("STENCIL_TUNE_CACHE")
+    b2 = st.Stencil(dim, r, c)
+    assert (b2.default_schedule((ny, nx)).t, b2.default_schedule((ny, nx)).seg) == (base.t, base.seg)
