@@ -53,6 +53,7 @@ extern "C" {
 #define STENCIL_ERR_CUDA         (-5) /* a CUDA runtime call failed */
 #define STENCIL_ERR_TIMEOUT      (-6) /* a kernel's bounded wait expired (device status) */
 #define STENCIL_ERR_NO_DEVICE    (-7) /* no usable GPU */
+#define STENCIL_ERR_BOUNDS       (-8) /* a bounds-checked kernel skipped an out-of-range access (device status) */
 
 typedef struct stencil_plan *stencil_handle;
 
@@ -263,8 +264,9 @@ typedef struct {
 int stencil_run_batched(const stencil_batch_item *items, int n, void *stream);
 
 /* Synchronise `stream`, then read and return the sticky device status of the
- * current device: STENCIL_OK, or STENCIL_ERR_TIMEOUT when a kernel gave up a
- * bounded wait (it then stopped early and its output is not valid).
+ * current device: STENCIL_OK, STENCIL_ERR_TIMEOUT when a kernel gave up a
+ * bounded wait (it then stopped early and its output is not valid), or
+ * STENCIL_ERR_BOUNDS when a bounds-checked kernel skipped an access.
  * `clear` != 0 resets the status to OK afterwards. */
 int stencil_get_device_status(void *stream, int clear);
 
@@ -277,6 +279,17 @@ int stencil_get_device_status(void *stream, int clear);
  * grids swept with this handle never report completion, so the bounded waits
  * of their next pass expire. */
 int stencil_set_fault_injection(stencil_handle h, int plane, int timeout_ms);
+
+/* Memory-checker substitute: with on = 1, streaming sweeps on this handle use
+ * the bounds-checked kernel instantiations, which test every shared-memory
+ * access, global store and TMA copy against its buffer and, instead of
+ * performing an out-of-range one, record STENCIL_ERR_BOUNDS in the device
+ * status (read with stencil_get_device_status).  Only a few configurations
+ * are compiled checked (2D FP32 r=1 t=1,5, r=4 t=2, r=6 t=2; 2D BF16 r=2
+ * t=3; 3D FP32 r=1 t=2 2 rows, r=3 t=1 4 rows, r=5 t=1 2 rows; 3D FP16 r=2
+ * t=1 2 rows); other schedules return UNSUPPORTED.  on = 0 restores the
+ * normal kernels.  Errors: INVALID_ARG. */
+int stencil_set_checked(stencil_handle h, int on);
 
 /* stencil_run without any device memory allocation, for callers that cannot
  * allocate: code that runs while a CUDA graph is being captured (where

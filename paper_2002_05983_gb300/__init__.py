@@ -23,6 +23,7 @@ STENCIL_ERR_OOM = -4
 STENCIL_ERR_CUDA = -5
 STENCIL_ERR_TIMEOUT = -6
 STENCIL_ERR_NO_DEVICE = -7
+STENCIL_ERR_BOUNDS = -8
 
 STENCIL_F32, STENCIL_BF16, STENCIL_F16 = 0, 1, 2
 KERNEL_AUTO, KERNEL_STREAM, KERNEL_NAIVE = 0, 1, 2
@@ -30,7 +31,7 @@ KERNEL_AUTO, KERNEL_STREAM, KERNEL_NAIVE = 0, 1, 2
 # every symbol include/stencil.h declares
 EXPORTS = ("stencil_create", "stencil_create_shared", "stencil_destroy", "stencil_run", "stencil_run_ex", "stencil_run_host",
            "stencil_default_schedule", "stencil_max_t", "stencil_get_device_status",
-           "stencil_set_fault_injection", "stencil_run_noalloc", "stencil_run_batched", "stencil_tune",
+           "stencil_set_fault_injection", "stencil_set_checked", "stencil_run_noalloc", "stencil_run_batched", "stencil_tune",
            "stencil_schedule_features", "stencil_model_create", "stencil_model_destroy",
            "stencil_model_train", "stencil_model_predict", "stencil_model_normalization",
            "stencil_model_params", "stencil_model_grad", "stencil_last_cuda_error", "stencil_strerror")
@@ -92,6 +93,7 @@ def _lib():
                 lib.stencil_max_t.argtypes = [i32, i32, i32, i32]
                 lib.stencil_get_device_status.argtypes = [vp, i32]
                 lib.stencil_set_fault_injection.argtypes = [vp, i32, i32]
+                lib.stencil_set_checked.argtypes = [vp, i32]
                 lib.stencil_run_noalloc.argtypes = [vp, vp, vp, i64, i64, i64, i32, i32, vp]
                 lib.stencil_run_batched.argtypes = [ctypes.POINTER(BatchItem), i32, vp]
                 fp = ctypes.POINTER(ctypes.c_float)
@@ -185,6 +187,11 @@ def stencil_max_t(dim, radius, dtype, rows_per_thread=2) -> int:
 def stencil_get_device_status(stream=None, clear: bool = False) -> int:
     """Raw status code (0 or STENCIL_ERR_TIMEOUT); does not raise on TIMEOUT."""
     return int(_lib().stencil_get_device_status(stream, 1 if clear else 0))
+
+
+def stencil_set_checked(h, on: bool = True) -> int:
+    """Use the bounds-checked kernel instantiations on this handle (see stencil.h)."""
+    return _check(_lib().stencil_set_checked(h, 1 if on else 0), "stencil_set_checked")
 
 
 def stencil_set_fault_injection(h, plane: int, timeout_ms: int = 50) -> int:

@@ -24,6 +24,8 @@
 struct stencil_plan {
     int dim = 0, r = 0, K = 0;
     int shared = 0;              // 1: one coefficient per distance (K = r + 1)
+    int checked = 0;             // 1: bounds-checked kernel instantiations (stencil_set_checked)
+    int kind() const { return shared + 2 * checked; }   // registry key of the kernel variant
     float c[stn::kMaxK] = {};
     void *scratch = nullptr;     // second grid of the ping-pong between passes
     size_t scratch_bytes = 0;
@@ -83,7 +85,7 @@ struct Registry {
                            stn::list_3d_f32_r6,  stn::list_2d_bf16_r5, stn::list_2d_bf16_r6,
                            stn::list_3d_bf16_r5, stn::list_3d_bf16_r6, stn::list_2d_f16_r5,
                            stn::list_2d_f16_r6,  stn::list_3d_f16_r5,  stn::list_3d_f16_r6,
-                           stn::list_2d_f32sh,   stn::list_3d_f32sh};
+                           stn::list_2d_f32sh,   stn::list_3d_f32sh,   stn::list_checked};
         for (L f : lists) {
             const stn::KernelEntry *e = nullptr;
             const int n = f(&e);
@@ -199,11 +201,11 @@ void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz,
     const Registry &reg = registry();
     stencil_schedule d{};
     // shared-coefficient stencils have FP32 streaming kernels only; other storage runs naive
-    const bool have = reg.max_t(h->dim, h->r, dtype, h->dim == 3 ? 2 : 1, h->shared) > 0;
+    const bool have = reg.max_t(h->dim, h->r, dtype, h->dim == 3 ? 2 : 1, h->kind()) > 0;
     d.kernel = (have && stream_applicable(dtype, nx)) ? STENCIL_KERNEL_STREAM : STENCIL_KERNEL_NAIVE;
     if (h->dim == 2) {
         static const int t2[stn::kMaxR + 1] = {0, 5, 3, 2, 2, 2, 2};
-        d.t = std::max(1, std::min(t2[h->r], reg.max_t(2, h->r, dtype, 1, h->shared)));
+        d.t = std::max(1, std::min(t2[h->r], reg.max_t(2, h->r, dtype, 1, h->kind())));
         d.threads_x = 128;
         d.threads_y = 1;
         d.rows_per_thread = 1;
@@ -289,7 +291,7 @@ bool fc_lookup(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dt
     if (!fc_sync()) return false;
     bool hit = false;
     for (const auto &e : g_fc)
-        if (e.gpu == gpu && e.dim == h->dim && e.r == h->r && e.sh == h->shared && e.dtype == dtype && e.nx == nx &&
+        if (e.gpu == gpu && e.dim == h->dim && e.r == h->r && e.sh == h->kind() && e.dtype == dtype && e.nx == nx &&
             e.ny == ny && e.nz == nz) {
             *out = e.s;
             hit = true;
@@ -305,10 +307,10 @@ void fc_store(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
     const char *path = fc_sync();
     if (!path) return;
     std::ofstream f(path, std::ios::app);
-    f << "v1 " << gpu << ' ' << h->dim << ' ' << h->r << ' ' << h->shared << ' ' << dtype << ' ' << nx << ' ' << ny
+    f << "v1 " << gpu << ' ' << h->dim << ' ' << h->r << ' ' << h->kind() << ' ' << dtype << ' ' << nx << ' ' << ny
       << ' ' << nz << ' ' << s.kernel << ' ' << s.t << ' ' << s.threads_x << ' ' << s.threads_y << ' '
       << s.rows_per_thread << ' ' << s.seg << ' ' << s.prefetch << '\n';
-    g_fc.push_back({gpu, h->dim, h->r, h->shared, dtype, nx, ny, nz, s});
+    g_fc.push_back({gpu, h->dim, h->r, h->kind(), dtype, nx, ny, nz, s});
 }
 
 // The schedule stencil_run uses when the caller gives none: the default rule, overridden
@@ -327,7 +329,7 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
 {
     const int D = h->dim, R = h->r;
     const int vy = D == 3 ? s.rows_per_thread : 1;
-    const stn::KernelEntry *e = registry().find(D, R, t, vy, dtype, h->shared, s.threads_x, D == 3 ? s.threads_y : 0);
+    const stn::KernelEntry *e = registry().find(D, R, t, vy, dtype, h->kind(), s.threads_x, D == 3 ? s.threads_y : 0);
     if (!e) return STENCIL_ERR_UNSUPPORTED;
     if (s.prefetch && s.prefetch != e->pf) return STENCIL_ERR_UNSUPPORTED;
     if (e->smem > static_cast<size_t>(dev.max_smem)) return STENCIL_ERR_UNSUPPORTED;
@@ -584,7 +586,7 @@ int resolve(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype
     out.threads_x = static_cast<int>(ps.block.x);
     out.threads_y = static_cast<int>(ps.block.y);
     out.seg = ps.a.seg;
-    const stn::KernelEntry *e = registry().find(h->dim, h->r, s.t, h->dim == 3 ? s.rows_per_thread : 1, dtype, h->shared,
+    const stn::KernelEntry *e = registry().find(h->dim, h->r, s.t, h->dim == 3 ? s.rows_per_thread : 1, dtype, h->kind(),
                                                 out.threads_x, out.threads_y);
     out.prefetch = e ? e->pf : 0;
     if (h->dim == 2) out.rows_per_thread = 1;
@@ -596,7 +598,7 @@ double analytic_ns(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, in
                    int occ)
 {
     const int D = h->dim, R = h->r, t = s.t;
-    const stn::KernelEntry *e = registry().find(D, R, t, D == 3 ? s.rows_per_thread : 1, dtype, h->shared, s.threads_x,
+    const stn::KernelEntry *e = registry().find(D, R, t, D == 3 ? s.rows_per_thread : 1, dtype, h->kind(), s.threads_x,
                                                 s.threads_y);
     if (!e) return 1e9;
     const double es = elem_bytes(dtype);
@@ -650,7 +652,7 @@ int candidates(const stencil_plan *h, int64_t ny, int64_t nz, int dtype, stencil
     const int *segs = h->dim == 2 ? segs2 : segs3;
     for (int vy : {2, 4}) {
         if (h->dim == 2 && vy == 4) break;
-        const int tmax = registry().max_t(h->dim, h->r, dtype, h->dim == 3 ? vy : 1, h->shared);
+        const int tmax = registry().max_t(h->dim, h->r, dtype, h->dim == 3 ? vy : 1, h->kind());
         for (int t = 1; t <= tmax; ++t)
             for (int k = 0; k < 5; ++k) {
                 if (segs[k] > ns) continue;
@@ -737,7 +739,7 @@ int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cuda
         // largest compiled degree <= the chosen one that divides iters
         int t = std::max(1, std::min(s.t, b.iters));
         while (t > 1 && (b.iters % t != 0 || !registry().find(h->dim, h->r, t, h->dim == 3 ? s.rows_per_thread : 1,
-                                                                b.dtype, h->shared, s.threads_x, s.threads_y)))
+                                                                b.dtype, h->kind(), s.threads_x, s.threads_y)))
             --t;
         s.t = t;
         Item x;
@@ -747,7 +749,7 @@ int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cuda
         x.rows = h->dim == 3 ? s.rows_per_thread : 1;
         int rc = plan_pass(h, b.nx, b.ny, b.nz, b.dtype, t, s, dev, x.ps, true);
         if (rc) return rc;
-        x.e = registry().find(h->dim, h->r, t, x.rows, b.dtype, h->shared, s.threads_x, s.threads_y);
+        x.e = registry().find(h->dim, h->r, t, x.rows, b.dtype, h->kind(), s.threads_x, s.threads_y);
         if (!x.e) return STENCIL_ERR_UNSUPPORTED;
         x.ps.a.timeout_ms = h->timeout_ms;
         it.push_back(x);
@@ -1018,6 +1020,14 @@ int stencil_get_device_status(void *stream, int clear)
     CK(cudaMemcpy(&word, dev->status, sizeof(word), cudaMemcpyDeviceToHost));
     if (clear) CK(cudaMemset(dev->status, 0, sizeof(unsigned)));
     if (word & stn::kStatusTimeout) return STENCIL_ERR_TIMEOUT;
+    if (word & stn::kStatusBounds) return STENCIL_ERR_BOUNDS;
+    return STENCIL_OK;
+}
+
+int stencil_set_checked(stencil_handle h, int on)
+{
+    if (!h || (on != 0 && on != 1)) return STENCIL_ERR_INVALID_ARG;
+    h->checked = on;
     return STENCIL_OK;
 }
 
@@ -1293,6 +1303,7 @@ const char *stencil_strerror(int code)
     case STENCIL_ERR_CUDA: return "CUDA call failed";
     case STENCIL_ERR_TIMEOUT: return "kernel bounded wait expired";
     case STENCIL_ERR_NO_DEVICE: return "no usable GPU";
+    case STENCIL_ERR_BOUNDS: return "bounds-checked kernel found an out-of-range access";
     default: return "unknown status";
     }
 }

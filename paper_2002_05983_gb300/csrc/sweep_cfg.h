@@ -10,6 +10,7 @@ constexpr int kMaxK = 2 * 3 * kMaxR + 1;   // coefficients of a 3D radius-6 sten
 constexpr int kSmemHeader = 1024;    // mbarriers + abort flag
 constexpr int kMaxDepthIn = 64;
 constexpr unsigned kStatusTimeout = 1u;
+constexpr unsigned kStatusBounds = 2u;   // a bounds-checked kernel found an access out of range
 // Unrolled-chunk sizes in FMA per thread (steps x levels x cells x (2*D*r+1)):
 // 3D kernels whose rotating chunk exceeds kRotMaxFma use shifting chunks of about
 // kChunkFma (see Geo::U).

@@ -349,7 +349,8 @@ template <int MAXT> struct GhostPlan {
 };
 
 template <int MAXT>
-__device__ __forceinline__ GhostPlan<MAXT> plan_ghost(const Ghost &g, int pw, int ox, int nx, int tid, int nthr)
+__device__ __forceinline__ GhostPlan<MAXT> plan_ghost(const Ghost &g, int pw, int ox, int nx, int tid, int nthr,
+                                                      int plane_cells = 0, unsigned *status = nullptr)
 {
     GhostPlan<MAXT> p;
 #pragma unroll
@@ -379,6 +380,13 @@ __device__ __forceinline__ GhostPlan<MAXT> plan_ghost(const Ghost &g, int pw, in
         }
         p.dst[j] = row * pw + 4 * col;
         p.src[j] = src;
+        if (status) {   // checked build: every task must stay inside the plane
+            const int s0 = src < 0 ? -src - 1 : src;
+            if (p.dst[j] < 0 || p.dst[j] + 4 > plane_cells || s0 < 0 || s0 + (src < 0 ? 1 : 4) > plane_cells) {
+                atomicOr(status, kStatusBounds);
+                p.dst[j] = -1;
+            }
+        }
     }
     return p;
 }
@@ -420,7 +428,7 @@ __device__ __forceinline__ void mbar_inval(uint32_t bar)
 // one thread block.  Returns false if a bounded wait expired (the device
 // status word is then set).  Leaves the block's shared memory free for the
 // next piece.
-template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH>
+template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH, bool CHK>
 __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepArgs &a, int col, int Z0, int Z1,
                                            unsigned char *smem)
 {
@@ -449,6 +457,22 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
+    // CHK (bounds-checked instantiations, a substitute for a memory checker): every
+    // shared-memory access must fall in the block's rings, every global store in the
+    // output grid, every copy inside its slot and the grid; a violation sets
+    // kStatusBounds in the device status and the access is skipped.
+    auto smem_ok = [&](const void *ptr, int bytes) -> bool {
+        if constexpr (!CHK) {
+            (void)ptr;
+            (void)bytes;
+            return true;
+        } else {
+            const unsigned char *q = static_cast<const unsigned char *>(ptr);
+            const bool ok = q >= smem + kSmemHeader && q + bytes <= smem + G::SMEM;
+            if (!ok) atomicOr(a.status, kStatusBounds);
+            return ok;
+        }
+    };
 
     // 2D: the coefficients live in per-thread registers (the empty asm hides that they
     // are uniform), so each FMA reads them from the register file instead of uniform
@@ -537,7 +561,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     constexpr bool SAME = F32S && G::PADIN == G::PAD32;   // input ring laid out like the FP32 rings
     constexpr int MT32 = cdiv((D == 3) ? G::PH * 2 * G::NV + 2 * R * (PW / 4) : 2 * G::NV, NTHR);
     constexpr int MTIN = cdiv((D == 3) ? G::PH * 2 * G::NV + 2 * R * (PWIN / 4) : 2 * G::NV, NTHR);
-    constexpr bool X4 = D == 2 && G::NV == 1;          // loop-form fill (GhostX4)
+    constexpr bool X4 = D == 2 && G::NV == 1 && !CHK;   // loop-form fill (GhostX4)
     const Ghost g32 = make_ghost(ox, oy, PW, G::PH, a.nx, (D == 3) ? a.ny : 1, R, FW);
     const bool gh_on = g32.ntask > 0;                  // block-uniform: tile touches an x or y edge
     GhostPlan<X4 ? 1 : MT32> gp32;
@@ -547,10 +571,10 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         gx32 = make_ghost_x4(ox, oy, PW, G::PH, a.nx, 1, R);
         gxin = F32S ? gx32 : make_ghost_x4(ox_in, oy, PWIN, G::PH, a.nx, 1, R);
     } else {
-        gp32 = plan_ghost<MT32>(g32, PW, ox, a.nx, tid, NTHR);
+        gp32 = plan_ghost<MT32>(g32, PW, ox, a.nx, tid, NTHR, PW * G::PH, CHK ? a.status : nullptr);
         if constexpr (!SAME) {
             const Ghost gin = make_ghost(ox_in, oy, PWIN, G::PH, a.nx, (D == 3) ? a.ny : 1, R, FW);
-            gpin = plan_ghost<MTIN>(gin, PWIN, ox_in, a.nx, tid, NTHR);
+            gpin = plan_ghost<MTIN>(gin, PWIN, ox_in, a.nx, tid, NTHR, PWIN * G::PH, CHK ? a.status : nullptr);
         }
     }
     (void)gp32;
@@ -577,12 +601,29 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         if (q == a.fault_plane) return;
         if constexpr (D == 2) {
             const int xa = max(ox_in, 0), xb = min(ox_in + PWIN, a.nx);
-            const uint32_t bytes = xb > xa ? static_cast<uint32_t>((xb - xa) * sizeof(S)) : 0u;
+            uint32_t bytes = xb > xa ? static_cast<uint32_t>((xb - xa) * sizeof(S)) : 0u;
+            if constexpr (CHK) {   // destination inside the slot, source inside the grid, 16-byte units
+                const int64_t src = static_cast<int64_t>(q) * a.nx + xa;
+                const bool ok = xa - ox_in >= 0 && (xa - ox_in) * sizeof(S) + bytes <= SLOTIN * sizeof(S) &&
+                                src >= 0 && src * sizeof(S) + bytes <= static_cast<int64_t>(a.nx) * a.ns * sizeof(S) &&
+                                bytes % 16 == 0 && (src * sizeof(S)) % 16 == 0 && ((xa - ox_in) * sizeof(S)) % 16 == 0;
+                if (!ok) {
+                    atomicOr(a.status, kStatusBounds);
+                    bytes = 0;
+                }
+            }
             mbar_arrive_expect_tx(bar, bytes);
             if (bytes)
                 bulk_load(smem_addr(dst + (xa - ox_in)),
                           static_cast<const S *>(a.in) + static_cast<int64_t>(q) * a.nx + xa, bytes, bar);
         } else {
+            if constexpr (CHK) {   // the box's x coordinate must be 16-byte aligned
+                if ((ox_in * static_cast<int>(sizeof(S))) % 16 != 0 || q < 0 || q >= a.ns) {
+                    atomicOr(a.status, kStatusBounds);
+                    mbar_arrive_expect_tx(bar, 0);
+                    return;
+                }
+            }
             mbar_arrive_expect_tx(bar, static_cast<uint32_t>(PWIN * G::PH * sizeof(S)));
             tma_load_3d(smem_addr(dst), tmap, ox_in, oy, q, bar);
         }
@@ -673,8 +714,13 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
             own32 = ring32(s - 1, rslot(s, J, 0)) + toff;
         }
         auto ld = [&](int row, int dx, float (&v)[4]) {
-            if constexpr (s == 1) Fmt<S>::load4(own_in + row * PWIN + dx, v);
-            else Fmt<float>::load4(own32 + row * PW + dx, v);
+            if constexpr (s == 1) {
+                if (smem_ok(own_in + row * PWIN + dx, 4 * sizeof(S))) Fmt<S>::load4(own_in + row * PWIN + dx, v);
+                else v[0] = v[1] = v[2] = v[3] = 0.f;
+            } else {
+                if (smem_ok(own32 + row * PW + dx, 16)) Fmt<float>::load4(own32 + row * PW + dx, v);
+                else v[0] = v[1] = v[2] = v[3] = 0.f;
+            }
         };
         float up[(D == 3) ? R : 1][4], dn[(D == 3) ? R : 1][4];
         (void)up;
@@ -746,13 +792,23 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                 S *o = gout + static_cast<int64_t>(p) * pstride;
 #pragma unroll
                 for (int vy = 0; vy < VY; ++vy)
-                    if (ystore[vy]) Fmt<S>::store4(o + vy * a.nx, res[vy]);
+                    if (ystore[vy]) {
+                        if constexpr (CHK) {   // inside the output grid, four whole cells of one row
+                            const int64_t e = (o + vy * a.nx) - static_cast<S *>(a.out);
+                            const int64_t total = static_cast<int64_t>(a.nx) * a.ny * a.nz;
+                            if (e < 0 || e + 4 > total || gx + 4 > a.nx) {
+                                atomicOr(a.status, kStatusBounds);
+                                continue;
+                            }
+                        }
+                        Fmt<S>::store4(o + vy * a.nx, res[vy]);
+                    }
             }
         } else {
             float *dst = ring32(s, rslot(s, J, 0)) + toff;
 #pragma unroll
             for (int vy = 0; vy < VY; ++vy) {
-                Fmt<float>::store4(dst + vy * PW, res[vy]);
+                if (smem_ok(dst + vy * PW, 16)) Fmt<float>::store4(dst + vy * PW, res[vy]);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) q[s][jn][vy][v] = res[vy][v];
             }
@@ -792,7 +848,10 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         if (tid == 0) consumed_hi = p;
         float v4[VY][4];
 #pragma unroll
-        for (int vy = 0; vy < VY; ++vy) Fmt<S>::load4(inb + J * SLOTIN + vy * PWIN, v4[vy]);
+        for (int vy = 0; vy < VY; ++vy) {
+            if (smem_ok(inb + J * SLOTIN + vy * PWIN, 4 * sizeof(S))) Fmt<S>::load4(inb + J * SLOTIN + vy * PWIN, v4[vy]);
+            else v4[vy][0] = v4[vy][1] = v4[vy][2] = v4[vy][3] = 0.f;
+        }
         if constexpr (D == 3 && VY > 1) clamp_rows(v4);
 #pragma unroll
         for (int vy = 0; vy < VY; ++vy)
@@ -908,7 +967,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
 // column b mod (ntx*nty), planes [j*seg, (j+1)*seg) with j = b / (ntx*nty),
 // so blocks running together cover neighbouring tiles of the same planes and
 // share their overlapping halo reads in L2.
-template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH>
+template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH, bool CHK>
 __device__ __forceinline__ bool sweep_block(const CUtensorMap *tmap, const SweepArgs &a, int b, unsigned char *smem)
 {
     const int cols = a.ntx * a.nty;
@@ -927,7 +986,7 @@ __device__ __forceinline__ bool sweep_block(const CUtensorMap *tmap, const Sweep
         const int col = static_cast<int>(w / a.ns);
         const int z0 = static_cast<int>(w - static_cast<int64_t>(col) * a.ns);
         const int z1 = static_cast<int>(min(static_cast<int64_t>(a.ns), z0 + (we - w)));
-        ok = sweep_tile<D, R, T, VY, S, TX, TY, SH>(tmap, a, col, z0, z1, smem);
+        ok = sweep_tile<D, R, T, VY, S, TX, TY, SH, CHK>(tmap, a, col, z0, z1, smem);
         w += z1 - z0;
     }
     return ok;
@@ -935,12 +994,12 @@ __device__ __forceinline__ bool sweep_block(const CUtensorMap *tmap, const Sweep
 
 // ------------------------------------------------------------------ kernels
 // One pass over the grid: block b sweeps its planes of the tile columns (sweep_block).
-template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH>
+template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH, bool CHK>
 __global__ void __launch_bounds__(TX *TY)
     sweep_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ SweepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    sweep_block<D, R, T, VY, S, TX, TY, SH>(&tmap, a, static_cast<int>(blockIdx.x), smem);
+    sweep_block<D, R, T, VY, S, TX, TY, SH, CHK>(&tmap, a, static_cast<int>(blockIdx.x), smem);
 }
 
 // Persistent sweep of many grids of one kernel class, all passes, from a device tile
@@ -978,7 +1037,7 @@ __device__ __forceinline__ void fence_proxy_async_global()
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH>
+template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH, bool CHK>
 __global__ void __launch_bounds__(TX *TY)
     sweep_persistent(const __grid_constant__ BatchArgs B)
 {
@@ -1024,7 +1083,7 @@ __global__ void __launch_bounds__(TX *TY)
         __syncthreads();
         if (!s_ok) break;
         const SweepArgs a = B.args[task];
-        const bool done = sweep_block<D, R, T, VY, S, TX, TY, SH>(D == 3 ? B.maps + task : nullptr, a, q - tk.first, smem);
+        const bool done = sweep_block<D, R, T, VY, S, TX, TY, SH, CHK>(D == 3 ? B.maps + task : nullptr, a, q - tk.first, smem);
         __syncthreads();
         if (tid == 0 && task != B.fault_task) {
             __threadfence();
