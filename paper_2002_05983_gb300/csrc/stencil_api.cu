@@ -571,8 +571,8 @@ int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny,
 // ------------------------------------------------------------------------
 // Schedule tuner: candidates, analytic model, features.
 constexpr double kFp32InstrRate = 152.0 * 128.0 * 2.07e9;   // FP32 lane instructions / s (nominal)
-constexpr double kFpEfficiency = 0.40;   // FMA issue share the sweep kernels reach with >= 20 warps/SM
-constexpr double kFullWarps = 20.0;      // resident warps per SM below which latency is exposed
+constexpr double kFpEfficiency = 0.42;   // FMA issue share the sweep kernels reach with >= 16 warps/SM
+constexpr double kFullWarps = 16.0;      // resident warps per SM below which latency is exposed
 constexpr double kHbmBytesPerS = 6792.1e9 * 0.92;           // measured copy bandwidth, achievable share
 
 // Resolve every field of a schedule for a problem (the pass of degree t).
