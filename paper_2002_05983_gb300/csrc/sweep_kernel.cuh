@@ -505,6 +505,10 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     const int toffin = prow0 * PWIN + xl + PADIN;      // own cell 0 in an input plane
     const int gx = gx0 + xl;
     const bool xstore = xl >= G::HTX && xl < G::HTX + G::CX && gx < a.nx;
+    // 2D radius 1: x neighbours by warp shuffles except on these lanes
+    constexpr bool SHX = D == 2 && R == 1;
+    const bool xedge = (tx & 31) == 0 || (tx & 31) == 31 || gx <= 0 || gx + 4 >= a.nx;
+    (void)xedge;
     bool ystore[VY];
 #pragma unroll
     for (int vy = 0; vy < VY; ++vy) {
@@ -738,10 +742,30 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         for (int vy = 0; vy < VY; ++vy) {
             // L[m] holds cells x0-4(m+1) .. x0-4m-1, Rr[m] cells x0+4(m+1) .. x0+4m+7
             float L[NV][4], Rr[NV][4];
+            if constexpr (SHX) {
+                // radius 1 needs one cell on each side: the neighbouring lanes' own cells
+                // of the same plane; warp-edge and grid-edge lanes read shared memory
+                // (the neighbouring warp's cells, or the clamp frame)
+                const float(&c0)[VY][4] = q[s - 1][jc];
+                float l3 = __shfl_up_sync(0xffffffffu, c0[vy][3], 1);
+                float r0 = __shfl_down_sync(0xffffffffu, c0[vy][0], 1);
+                if (xedge) {
+                    float t4[4];
+                    ld(vy, -4, t4);
+                    l3 = t4[3];
+                    ld(vy, 4, t4);
+                    r0 = t4[0];
+                }
 #pragma unroll
-            for (int m = 0; m < NV; ++m) {
-                ld(vy, -4 * (m + 1), L[m]);
-                ld(vy, 4 * (m + 1), Rr[m]);
+                for (int v = 0; v < 4; ++v) L[0][v] = Rr[0][v] = 0.f;
+                L[0][3] = l3;
+                Rr[0][0] = r0;
+            } else {
+#pragma unroll
+                for (int m = 0; m < NV; ++m) {
+                    ld(vy, -4 * (m + 1), L[m]);
+                    ld(vy, 4 * (m + 1), Rr[m]);
+                }
             }
             const float(&ctr)[VY][4] = q[s - 1][jc];
 #pragma unroll
