@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -205,6 +206,21 @@ def traffic_for(dim, r, t, dtype="f32"):
     return None
 
 
+def host_cpu():
+    """CPU model (from /proc/cpuinfo, else the machine type) and the CPUs this process may use."""
+    model = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": model, "cpus_allowed": len(os.sched_getaffinity(0))}
+
+
 def oracle_leg(steps: int, warmup: int):
     """Time the CPU oracle on the crop; returns (GCell/s, seconds per step, cores, sample text)."""
     import oracle
@@ -240,7 +256,7 @@ def reference_main(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": sample, "l2": "n/a (host)"},
             "cpu_baseline": {"value": round(g, 4), "unit": "GCell/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu": host_cpu()},
             "e2e": {"value": round(g, 4), "unit": "GCell/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -662,7 +678,7 @@ def main():
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         g, dt, cores, sample = oracle_leg(1, 0)
         line["cpu_baseline"] = {"value": round(g, 4), "unit": "GCell/s", "cores": cores, "kind": "oracle",
-                                "sample": sample}
+                                "sample": sample, "cpu": host_cpu()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
