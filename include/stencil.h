@@ -140,8 +140,9 @@ int stencil_create_shared(stencil_handle *out, int dim, int radius, const float 
 int stencil_destroy(stencil_handle h);
 
 /* `iters` steps from `in` to `out` (device pointers, nx*ny*nz elements of
- * `dtype`), with the schedule the library picks (tuned schedule if
- * stencil_tune has stored one for this shape, else the analytic choice).
+ * `dtype`), with the schedule stencil_default_schedule reports (a pick that
+ * stencil_tune stored on the handle, else one in the tuning-cache file, else
+ * the library's rule).
  * iters == 0 copies in to out.  Errors: INVALID_ARG (sizes <= 0, dim 2 with
  * nz != 1, NULL pointers, iters < 0, bad dtype), ALIAS, OOM, CUDA. */
 int stencil_run(stencil_handle h, const void *in, void *out, int64_t nx, int64_t ny,
