@@ -1,4 +1,4 @@
-"""GB300-native repeated star-stencil sweeps (2D/3D, radius 1..4, clamp to edge).
+"""GB300-native repeated star-stencil sweeps (2D/3D, radius 1..6, per-direction or shared coefficients, clamp to edge).
 
 A thin ctypes binding over libstencil.so (the C ABI declared in
 include/stencil.h).  The functions below carry the C names and only marshal
