@@ -91,6 +91,9 @@ typedef struct {
     int rows_per_thread; /* 3D: 2 or 4 */
     int seg;             /* stream-axis rows/planes per block, >= 1 */
     int prefetch;        /* 0, or the compiled number of planes loaded ahead */
+    int planes_per_step; /* 2D: rows every time level advances per step of the block's loop,
+                            1 or 2 (two rows share one barrier and one copy wait); 3D: 1.
+                            A degree compiled with one row per step only runs with one. */
 } stencil_schedule;
 
 /* Number of features describing one (problem, schedule) pair for the cost model. */

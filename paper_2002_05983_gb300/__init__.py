@@ -51,7 +51,7 @@ class Schedule(ctypes.Structure):
     """stencil_schedule: 0 in any field = chosen by the library."""
     _fields_ = [("kernel", ctypes.c_int), ("t", ctypes.c_int), ("threads_x", ctypes.c_int),
                 ("threads_y", ctypes.c_int), ("rows_per_thread", ctypes.c_int), ("seg", ctypes.c_int),
-                ("prefetch", ctypes.c_int)]
+                ("prefetch", ctypes.c_int), ("planes_per_step", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -85,27 +85,29 @@ struct Registry {
                            stn::list_3d_f32_r6,  stn::list_2d_bf16_r5, stn::list_2d_bf16_r6,
                            stn::list_3d_bf16_r5, stn::list_3d_bf16_r6, stn::list_2d_f16_r5,
                            stn::list_2d_f16_r6,  stn::list_3d_f16_r5,  stn::list_3d_f16_r6,
-                           stn::list_2d_f32sh,   stn::list_3d_f32sh,   stn::list_checked};
+                           stn::list_2d_f32sh,   stn::list_3d_f32sh,   stn::list_checked,  stn::list_2d_f32_p2,
+                           stn::list_2d_bf16_p2, stn::list_2d_f16_p2};
         for (L f : lists) {
             const stn::KernelEntry *e = nullptr;
             const int n = f(&e);
             all.insert(all.end(), e, e + n);
         }
     }
-    // tx / ty = 0: the default block shape (the first listed for that degree)
-    const stn::KernelEntry *find(int dim, int r, int t, int vy, int dtype, int sh, int tx = 0, int ty = 0) const
+    // tx / ty = 0: the default block shape (the first listed for that degree); p: planes per step
+    const stn::KernelEntry *find(int dim, int r, int t, int vy, int dtype, int sh, int tx = 0, int ty = 0,
+                                 int p = 1) const
     {
         for (const auto &e : all)
             if (e.dim == dim && e.r == r && e.t == t && (dim == 2 || e.vy == vy) && e.dtype == dtype &&
-                e.sh == sh && (!tx || e.tx == tx) && (dim == 2 || !ty || e.ty == ty))
+                e.sh == sh && (!tx || e.tx == tx) && (dim == 2 || !ty || e.ty == ty) && e.p == p)
                 return &e;
         return nullptr;
     }
-    int max_t(int dim, int r, int dtype, int vy, int sh) const
+    int max_t(int dim, int r, int dtype, int vy, int sh, int p = 1) const
     {
         int m = 0;
         for (const auto &e : all)
-            if (e.dim == dim && e.r == r && e.dtype == dtype && (dim == 2 || e.vy == vy) && e.sh == sh)
+            if (e.dim == dim && e.r == r && e.dtype == dtype && (dim == 2 || e.vy == vy) && e.sh == sh && e.p == p)
                 m = std::max(m, e.t);
         return m;
     }
@@ -180,6 +182,7 @@ int round_up(int a, int m) { return (a + m - 1) / m * m; }
 
 struct Pass {
     const void *fn = nullptr;
+    const stn::KernelEntry *e = nullptr;   // the kernel's registry entry
     int t = 0;
     int occ = 0;   // resident blocks per SM
     int padin = 0; // input-plane x padding per side: 3D tensor-map box width 4*block.x + 2*padin
@@ -204,16 +207,20 @@ void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz,
     const bool have = reg.max_t(h->dim, h->r, dtype, h->dim == 3 ? 2 : 1, h->kind()) > 0;
     d.kernel = (have && stream_applicable(dtype, nx)) ? STENCIL_KERNEL_STREAM : STENCIL_KERNEL_NAIVE;
     if (h->dim == 2) {
-        static const int t2[stn::kMaxR + 1] = {0, 5, 3, 2, 2, 2, 2};
+        // measured on 16384^2 FP32: radius 1 peaks at t = 4 with one row per step; radii
+        // 2-4 gain 12-19 % from two rows per step (t = 3, 2, 2)
+        static const int t2[stn::kMaxR + 1] = {0, 4, 3, 2, 2, 2, 2};
         d.t = std::max(1, std::min(t2[h->r], reg.max_t(2, h->r, dtype, 1, h->kind())));
         d.threads_x = 128;
         d.threads_y = 1;
         d.rows_per_thread = 1;
+        d.planes_per_step = h->r >= 2 && reg.find(2, h->r, d.t, 1, dtype, h->kind(), 128, 0, 2) ? 2 : 1;
     } else {
         d.t = h->r == 1 ? 2 : 1;
         d.rows_per_thread = 2;
         d.threads_x = 16;
         d.threads_y = 8;
+        d.planes_per_step = 1;
     }
     d.seg = 0;
     d.prefetch = 0;
@@ -221,8 +228,9 @@ void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz,
 }
 
 // ---- persistent tuning cache: the file named by STENCIL_TUNE_CACHE holds one line per
-// stored pick, "v1 <gpu> <dim> <r> <shared> <dtype> <nx> <ny> <nz> <kernel> <t> <threads_x>
-// <threads_y> <rows> <seg> <prefetch>", the last line for a key winning.  A pick is keyed by
+// stored pick, "v2 <gpu> <dim> <r> <shared> <dtype> <nx> <ny> <nz> <kernel> <t> <threads_x>
+// <threads_y> <rows> <seg> <prefetch> <planes_per_step>", the last line for a key winning
+// (v1 lines, without the last field, are read as one plane per step).  A pick is keyed by
 // the GPU's name and the problem (not the coefficients, which do not change the speed).
 struct FileCacheEntry {
     std::string gpu;
@@ -275,8 +283,10 @@ const char *fc_sync()
             FileCacheEntry e{};
             if (!(is >> v >> e.gpu >> e.dim >> e.r >> e.sh >> e.dtype >> e.nx >> e.ny >> e.nz >> e.s.kernel >> e.s.t >>
                   e.s.threads_x >> e.s.threads_y >> e.s.rows_per_thread >> e.s.seg >> e.s.prefetch) ||
-                v != "v1")
+                (v != "v1" && v != "v2"))
                 continue;   // not a cache line
+            e.s.planes_per_step = 1;
+            if (v == "v2" && !(is >> e.s.planes_per_step)) continue;
             g_fc.push_back(e);
         }
     }
@@ -307,9 +317,9 @@ void fc_store(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
     const char *path = fc_sync();
     if (!path) return;
     std::ofstream f(path, std::ios::app);
-    f << "v1 " << gpu << ' ' << h->dim << ' ' << h->r << ' ' << h->kind() << ' ' << dtype << ' ' << nx << ' ' << ny
+    f << "v2 " << gpu << ' ' << h->dim << ' ' << h->r << ' ' << h->kind() << ' ' << dtype << ' ' << nx << ' ' << ny
       << ' ' << nz << ' ' << s.kernel << ' ' << s.t << ' ' << s.threads_x << ' ' << s.threads_y << ' '
-      << s.rows_per_thread << ' ' << s.seg << ' ' << s.prefetch << '\n';
+      << s.rows_per_thread << ' ' << s.seg << ' ' << s.prefetch << ' ' << s.planes_per_step << '\n';
     g_fc.push_back({gpu, h->dim, h->r, h->kind(), dtype, nx, ny, nz, s});
 }
 
@@ -329,7 +339,12 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
 {
     const int D = h->dim, R = h->r;
     const int vy = D == 3 ? s.rows_per_thread : 1;
-    const stn::KernelEntry *e = registry().find(D, R, t, vy, dtype, h->kind(), s.threads_x, D == 3 ? s.threads_y : 0);
+    int pps = D == 2 && s.planes_per_step ? s.planes_per_step : 1;
+    const stn::KernelEntry *e = registry().find(D, R, t, vy, dtype, h->kind(), s.threads_x, D == 3 ? s.threads_y : 0, pps);
+    if (!e && pps == 2) {   // a degree compiled with one row per step only (e.g. a remainder pass)
+        pps = 1;
+        e = registry().find(D, R, t, vy, dtype, h->kind(), s.threads_x, 0, 1);
+    }
     if (!e) return STENCIL_ERR_UNSUPPORTED;
     if (s.prefetch && s.prefetch != e->pf) return STENCIL_ERR_UNSUPPORTED;
     if (e->smem > static_cast<size_t>(dev.max_smem)) return STENCIL_ERR_UNSUPPORTED;
@@ -344,7 +359,7 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
     const int64_t ns = D == 3 ? nz : ny;
     const int64_t tiles = ntx * nty;
     const int64_t slots = static_cast<int64_t>(dev.sms) * occ;
-    const int64_t minseg = std::max<int64_t>(64, 8 * t * (2 * R + 1));
+    const int64_t minseg = std::max<int64_t>(64, 8 * t * (2 * R + pps));
     // Two block orders.  Slabs: the stream axis is cut into slabs of seg planes,
     // the tiles of one slab in consecutive blocks, so blocks that run together
     // read neighbouring tiles of the same rows/planes (DRAM locality, shared halo
@@ -377,6 +392,7 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
     if (nblk > 0x7fffffffLL || seg > 0x7fffffffLL) return STENCIL_ERR_UNSUPPORTED;
 
     ps.fn = e->fn;
+    ps.e = e;
     ps.t = t;
     ps.occ = occ;
     ps.grid = dim3(static_cast<unsigned>(nblk));
@@ -512,7 +528,9 @@ int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny,
         if (user->rows_per_thread) s.rows_per_thread = user->rows_per_thread;
         if (user->seg) s.seg = user->seg;
         if (user->prefetch) s.prefetch = user->prefetch;
-        if (s.t < 0 || s.seg < 0 || s.prefetch < 0) return STENCIL_ERR_INVALID_ARG;
+        if (user->planes_per_step) s.planes_per_step = user->planes_per_step;
+        if (s.t < 0 || s.seg < 0 || s.prefetch < 0 || s.planes_per_step < 0 || s.planes_per_step > 2)
+            return STENCIL_ERR_INVALID_ARG;
         if (h->dim == 3 && user->t && !user->rows_per_thread)
             s.rows_per_thread = 2;
     }
@@ -586,9 +604,8 @@ int resolve(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype
     out.threads_x = static_cast<int>(ps.block.x);
     out.threads_y = static_cast<int>(ps.block.y);
     out.seg = ps.a.seg;
-    const stn::KernelEntry *e = registry().find(h->dim, h->r, s.t, h->dim == 3 ? s.rows_per_thread : 1, dtype, h->kind(),
-                                                out.threads_x, out.threads_y);
-    out.prefetch = e ? e->pf : 0;
+    out.prefetch = ps.e->pf;
+    out.planes_per_step = ps.e->p;
     if (h->dim == 2) out.rows_per_thread = 1;
     return 0;
 }
@@ -599,7 +616,7 @@ double analytic_ns(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, in
 {
     const int D = h->dim, R = h->r, t = s.t;
     const stn::KernelEntry *e = registry().find(D, R, t, D == 3 ? s.rows_per_thread : 1, dtype, h->kind(), s.threads_x,
-                                                s.threads_y);
+                                                s.threads_y, D == 2 && s.planes_per_step ? s.planes_per_step : 1);
     if (!e) return 1e9;
     const double es = elem_bytes(dtype);
     const double N = static_cast<double>(nx) * ny * nz;
@@ -654,15 +671,19 @@ int candidates(const stencil_plan *h, int64_t ny, int64_t nz, int dtype, stencil
         if (h->dim == 2 && vy == 4) break;
         const int tmax = registry().max_t(h->dim, h->r, dtype, h->dim == 3 ? vy : 1, h->kind());
         for (int t = 1; t <= tmax; ++t)
-            for (int k = 0; k < 5; ++k) {
-                if (segs[k] > ns) continue;
-                if (n >= cap) return n;
-                stencil_schedule s{};
-                s.kernel = STENCIL_KERNEL_STREAM;
-                s.t = t;
-                s.rows_per_thread = h->dim == 3 ? vy : 1;
-                s.seg = segs[k];
-                out[n++] = s;
+            for (int pps = 1; pps <= (h->dim == 2 ? 2 : 1); ++pps) {
+                if (pps == 2 && !registry().find(2, h->r, t, 1, dtype, h->kind(), 0, 0, 2)) continue;
+                for (int k = 0; k < 5; ++k) {
+                    if (segs[k] > ns) continue;
+                    if (n >= cap) return n;
+                    stencil_schedule s{};
+                    s.kernel = STENCIL_KERNEL_STREAM;
+                    s.t = t;
+                    s.rows_per_thread = h->dim == 3 ? vy : 1;
+                    s.seg = segs[k];
+                    s.planes_per_step = pps;
+                    out[n++] = s;
+                }
             }
     }
     return n;
@@ -749,8 +770,7 @@ int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cuda
         x.rows = h->dim == 3 ? s.rows_per_thread : 1;
         int rc = plan_pass(h, b.nx, b.ny, b.nz, b.dtype, t, s, dev, x.ps, true);
         if (rc) return rc;
-        x.e = registry().find(h->dim, h->r, t, x.rows, b.dtype, h->kind(), s.threads_x, s.threads_y);
-        if (!x.e) return STENCIL_ERR_UNSUPPORTED;
+        x.e = x.ps.e;
         x.ps.a.timeout_ms = h->timeout_ms;
         it.push_back(x);
     }
@@ -1201,8 +1221,8 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
     DevInfo *dev = nullptr;
     int rc = device_info(&dev);
     if (rc) return rc;
-    stencil_schedule cand[256];
-    const int nc0 = candidates(h, ny, nz, dtype, cand, 256);
+    stencil_schedule cand[512];
+    const int nc0 = candidates(h, ny, nz, dtype, cand, 512);
     std::vector<stencil_timing> tim;
     std::vector<Pass> passes;
     for (int i = 0; i < nc0; ++i) {
@@ -1211,7 +1231,9 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
         if (resolve(h, nx, ny, nz, dtype, cand[i], *dev, r, ps)) continue;   // tile too small etc.
         bool dup = false;   // several requested segment lengths can resolve to the same one
         for (const auto &x : tim)
-            if (x.sched.t == r.t && x.sched.seg == r.seg && x.sched.rows_per_thread == r.rows_per_thread) dup = true;
+            if (x.sched.t == r.t && x.sched.seg == r.seg && x.sched.rows_per_thread == r.rows_per_thread &&
+                x.sched.planes_per_step == r.planes_per_step)
+                dup = true;
         if (dup) continue;
         stencil_timing tm{};
         tm.sched = r;

@@ -1,0 +1,30 @@
+// Streaming-kernel instantiations: float storage, 2D, 128 threads x 4 cells per block row,
+// two rows per step (every level advances two rows between barriers, so the per-step
+// bookkeeping, copy wait and barrier are shared by two rows).
+#include "registry.h"
+#include "sweep_kernel.cuh"
+
+namespace stn {
+namespace {
+const KernelEntry kList[] = {
+    STN_EP(2, 1, 2, float, 0, 2),
+    STN_EP(2, 1, 3, float, 0, 2),
+    STN_EP(2, 1, 4, float, 0, 2),
+    STN_EP(2, 1, 5, float, 0, 2),
+    STN_EP(2, 2, 1, float, 0, 2),
+    STN_EP(2, 2, 2, float, 0, 2),
+    STN_EP(2, 2, 3, float, 0, 2),
+    STN_EP(2, 2, 4, float, 0, 2),
+    STN_EP(2, 3, 1, float, 0, 2),
+    STN_EP(2, 3, 2, float, 0, 2),
+    STN_EP(2, 3, 3, float, 0, 2),
+    STN_EP(2, 4, 1, float, 0, 2),
+    STN_EP(2, 4, 2, float, 0, 2),
+    STN_EP(2, 4, 3, float, 0, 2)};
+}  // namespace
+int list_2d_f32_p2(const KernelEntry **e)
+{
+    *e = kList;
+    return static_cast<int>(sizeof(kList) / sizeof(kList[0]));
+}
+}  // namespace stn

@@ -21,9 +21,10 @@ __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr int rup(int a, int b) { return cdiv(a, b) * b; }
 
 // D: 2 or 3; R: radius; T: time levels per pass; VY: y rows per thread (3D);
-// ES: bytes per stored element (4 fp32, 2 bf16/fp16); TX x TY threads.
-template <int D, int R, int T, int VY, int ES, int TX, int TY> struct Geo {
-    static constexpr int QP = 2 * R + 1;               // register-queue period
+// ES: bytes per stored element (4 fp32, 2 bf16/fp16); TX x TY threads;
+// P: planes every level advances per step (rows in 2D; 1 in 3D).
+template <int D, int R, int T, int VY, int ES, int TX, int TY, int P = 1> struct Geo {
+    static_assert(P == 1 || (P == 2 && D == 2), "two planes per step are a 2D schedule");
     static constexpr bool F32S = ES == 4;
     static constexpr int NV = cdiv(R, 4);              // 4-cell vectors of x neighbours per side
     static constexpr int ALIGN = 16 / ES;              // cells per 16 bytes of storage
@@ -40,9 +41,20 @@ template <int D, int R, int T, int VY, int ES, int TX, int TY> struct Geo {
     static constexpr int PWIN = BX + 2 * PADIN;        // input plane row (elements)
     static constexpr int SLOT32 = rup(PW * PH, 32);    // floats per FP32 ring slot
     static constexpr int SLOTIN = rup(PWIN * PH * ES, 128) / ES;   // elements per input slot
-    static constexpr int PFMIN = (D == 2) ? 4 : 2;
-    // Steps per unrolled chunk.  The register queue of a level holds 2r+1 planes;
-    // with U = QP steps per chunk it rotates through fixed registers (ROT).  In
+    // Plane lags.  Level s handles planes P*k - lag(s) + j (j < P) at step k.  Level 1
+    // trails the input by L1 >= R planes (its stream-axis neighbours are in registers) and
+    // by >= P planes (the input planes it reads in shared memory had their clamp frame
+    // written in an earlier step); each further level trails the one below by GAP = P +
+    // max(R, P): the r planes ahead it needs were computed in an earlier step, and the
+    // planes it reads in shared memory had their clamp frame filled an earlier step still.
+    static constexpr int L1 = R > P ? R : P;
+    static constexpr int GAP = P + L1;
+    // A level's register queue (and FP32 ring) spans the GAP + R planes the level above
+    // reads in one step, rounded up to whole steps: plane p sits in slot p mod QP.
+    static constexpr int QP = rup(GAP + R, P);
+    static constexpr int PFMIN = (D == 2) ? 4 : 2;     // planes loaded ahead at least
+    // Steps per unrolled chunk.  The register queue of a level holds QP planes;
+    // with U = QP / P steps per chunk it rotates through fixed registers (ROT).  In
     // 3D, a rotating chunk larger than kRotMaxFma misses the instruction cache, so
     // chunks of U < QP steps append to a queue of QP + U registers and shift it
     // down by U planes at the chunk's end (QP moves per cell and level every U
@@ -50,20 +62,23 @@ template <int D, int R, int T, int VY, int ES, int TX, int TY> struct Geo {
     // queue at every size: there the moves cost more than the misses they avoid.
     static constexpr int BODY = T * VY * 4 * (2 * D * R + 1);
     static constexpr bool ROT = D == 2 || QP * BODY <= kRotMaxFma;
-    static constexpr int U = ROT ? QP : (kChunkFma / BODY >= 1 ? kChunkFma / BODY : 1);
+    static constexpr int U = ROT ? QP / P : (kChunkFma / BODY >= 1 ? kChunkFma / BODY : 1);
     static constexpr int NQ = ROT ? QP : QP + U;       // queue registers per level and cell
-    static constexpr int LAG1 = R;                     // steps level 1 trails the input
-    static constexpr int KEEP = R + 1;                 // input slots held besides prefetch
-    static constexpr int DEPTH = U * cdiv(KEEP + PFMIN, U);     // input ring slots (chunk multiple)
-    static constexpr int PF = DEPTH - KEEP;            // planes loaded ahead of use
+    // Input ring in steps of P planes: the step that level 1 reads in shared memory lags
+    // the newest by KS = ceil(L1 / P) steps; PFS steps are loaded ahead.
+    static constexpr int KS = cdiv(L1, P);
+    static constexpr int DS = U * cdiv(KS + 1 + cdiv(PFMIN, P), U);   // step slots (chunk multiple)
+    static constexpr int PFS = DS - KS - 1;            // steps loaded ahead of use
+    static constexpr int PF = P * PFS;                 // planes loaded ahead of use
+    static constexpr int DEPTH = P * DS;               // input ring slots (planes)
     static constexpr int NRING = T - 1;                // FP32 rings written by levels 1..T-1
     static constexpr size_t SMEM = static_cast<size_t>(kSmemHeader) +
                                    static_cast<size_t>(DEPTH) * SLOTIN * ES +
                                    static_cast<size_t>(NRING) * QP * SLOT32 * 4;
-    static constexpr bool OK = CX >= 8 && CY >= 1 && DEPTH <= kMaxDepthIn &&
+    static constexpr bool OK = CX >= 8 && CY >= 1 && DS <= kMaxDepthIn &&
                                (D == 2 || (PWIN <= 256 && PH <= 256));
-    // step at which level s handles plane p: p + lag(s)
-    __host__ __device__ static constexpr int lag(int s) { return s == 0 ? 0 : LAG1 + (s - 1) * (R + 1); }
+    // plane lag of level s (plane p of level s is handled at step (p + lag(s)) / P)
+    __host__ __device__ static constexpr int lag(int s) { return s == 0 ? 0 : L1 + (s - 1) * GAP; }
 };
 
 }  // namespace stn

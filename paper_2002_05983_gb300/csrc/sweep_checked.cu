@@ -9,15 +9,15 @@
 namespace stn {
 namespace {
 const KernelEntry kList[] = {
-    STN_EXC(2, 1, 1, 1, float, 0, 128, 1, false, true),
-    STN_EXC(2, 1, 5, 1, float, 0, 128, 1, false, true),
-    STN_EXC(2, 4, 2, 1, float, 0, 128, 1, false, true),
-    STN_EXC(2, 6, 2, 1, float, 0, 128, 1, false, true),
-    STN_EXC(2, 2, 3, 1, __nv_bfloat16, 1, 128, 1, false, true),
-    STN_EXC(3, 1, 2, 2, float, 0, 16, 8, false, true),
-    STN_EXC(3, 3, 1, 4, float, 0, 16, 8, false, true),
-    STN_EXC(3, 5, 1, 2, float, 0, 16, 8, false, true),
-    STN_EXC(3, 2, 1, 2, __half, 2, 16, 8, false, true)};
+    STN_EXC(2, 1, 1, 1, float, 0, 128, 1, false, true, 1),
+    STN_EXC(2, 1, 5, 1, float, 0, 128, 1, false, true, 1),
+    STN_EXC(2, 4, 2, 1, float, 0, 128, 1, false, true, 1),
+    STN_EXC(2, 6, 2, 1, float, 0, 128, 1, false, true, 1),
+    STN_EXC(2, 2, 3, 1, __nv_bfloat16, 1, 128, 1, false, true, 1),
+    STN_EXC(3, 1, 2, 2, float, 0, 16, 8, false, true, 1),
+    STN_EXC(3, 3, 1, 4, float, 0, 16, 8, false, true, 1),
+    STN_EXC(3, 5, 1, 2, float, 0, 16, 8, false, true, 1),
+    STN_EXC(3, 2, 1, 2, __half, 2, 16, 8, false, true, 1)};
 }  // namespace
 int list_checked(const KernelEntry **e)
 {

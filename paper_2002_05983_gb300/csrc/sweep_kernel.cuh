@@ -428,11 +428,11 @@ __device__ __forceinline__ void mbar_inval(uint32_t bar)
 // one thread block.  Returns false if a bounded wait expired (the device
 // status word is then set).  Leaves the block's shared memory free for the
 // next piece.
-template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH, bool CHK>
+template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH, bool CHK, int P>
 __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepArgs &a, int col, int Z0, int Z1,
                                            unsigned char *smem)
 {
-    using G = Geo<D, R, T, VY, static_cast<int>(sizeof(S)), TX, TY>;
+    using G = Geo<D, R, T, VY, static_cast<int>(sizeof(S)), TX, TY, P>;
     static_assert(D == 2 || D == 3, "dim");
     static_assert(R >= 1 && R <= kMaxR, "radius");
     static_assert(D == 3 || (VY == 1 && TY == 1), "2D keeps one row per thread");
@@ -445,7 +445,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     constexpr int K2 = 2 * D;
     constexpr int PW = G::PW, PWIN = G::PWIN;
     constexpr int NTHR = TX * TY;
-    constexpr int DEPTH = G::DEPTH;
+    constexpr int DEPTH = G::DEPTH, DS = G::DS;
     constexpr int SLOT32 = G::SLOT32, SLOTIN = G::SLOTIN;
 
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
@@ -543,21 +543,24 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         }
     };
 
-    // ---- plane ranges: level s covers planes [lo[s], hi[s]], plane p at step p + lag(s)
+    // ---- plane ranges: level s covers planes [lo[s], hi[s]]; step k handles its planes
+    // P*k - lag(s) + j, j < P
+    auto fdiv = [](int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
     int lo[T + 1], hi[T + 1];
     int kA = 0, kB = 0x7fffffff;
 #pragma unroll
     for (int s = 0; s <= T; ++s) {
         lo[s] = max(Z0 - (T - s) * R, 0);
         hi[s] = Z1 - 1 + (T - s) * R;
-        kA = max(kA, max(lo[s], 1) + G::lag(s));
-        kB = min(kB, min(hi[s], last) + G::lag(s));
+        kA = max(kA, cdiv(max(lo[s], 1) + G::lag(s), P));
+        kB = min(kB, fdiv(min(hi[s], last) + G::lag(s) + 1 - P, P));
     }
-    // steps in [kA, kB] have every level active, inside the grid and past plane 0
-    const int k0 = lo[0];
-    const int k1 = Z1 - 1 + G::lag(T);
+    // steps in [kA, kB] have every plane of every level active, inside the grid and past plane 0
+    const int k0 = lo[0] / P;                          // first step (level 0 loads plane lo[0])
+    const int k1 = (Z1 - 1 + G::lag(T)) / P;           // last step (level T stores plane Z1 - 1)
     const int lmax = min(hi[0], last);                 // last input plane to load
-    const int lap0 = k0 / DEPTH;
+    const int smax = lmax / P;                         // last step with an input plane to load
+    const int lap0 = k0 / DS;
 
     // clamp frames (x: the 4*NV cells the neighbour loads reach; 3D y: r rows) of the
     // FP32 rings and of the input ring, each thread's tasks resolved once per tile
@@ -587,40 +590,47 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     (void)gxin;
 
     if (tid == 0) {
-        for (int i = 0; i < DEPTH; ++i) mbar_init(smem_addr(bars + i), 1);
-        // slots before k0's slot are first used one lap later: retire their phase 0 now
-        for (int i = 0; i < k0 % DEPTH; ++i) mbar_arrive(smem_addr(bars + i));
+        for (int i = 0; i < DS; ++i) mbar_init(smem_addr(bars + i), 1);
+        // step slots before k0's slot are first used one lap later: retire their phase 0 now
+        for (int i = 0; i < k0 % DS; ++i) mbar_arrive(smem_addr(bars + i));
         *sflag = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
-    // thread 0 issues the input loads; plane q goes to slot q mod DEPTH
+    // thread 0 issues the input loads: step kq brings planes P*kq + j (j < P, up to lmax)
+    // into the P slots of step slot kq mod DS, completing one mbarrier phase
     int issued_hi = k0 - 1;
-    auto issue = [&](int q) {
-        const int slot = q % DEPTH;
-        const uint32_t bar = smem_addr(bars + slot);
-        S *dst = ring_in + slot * SLOTIN;
-        issued_hi = q;
-        if (q == a.fault_plane) return;
+    auto issue = [&](int kq) {
+        const int sslot = kq % DS;
+        const uint32_t bar = smem_addr(bars + sslot);
+        S *dst0 = ring_in + sslot * P * SLOTIN;
+        issued_hi = kq;
+        if (a.fault_plane >= P * kq && a.fault_plane < P * kq + P) return;   // test hook: never complete
         if constexpr (D == 2) {
             const int xa = max(ox_in, 0), xb = min(ox_in + PWIN, a.nx);
             uint32_t bytes = xb > xa ? static_cast<uint32_t>((xb - xa) * sizeof(S)) : 0u;
+            const int nq = P == 1 ? 1 : min(P, lmax - P * kq + 1);   // planes of this step inside the grid
             if constexpr (CHK) {   // destination inside the slot, source inside the grid, 16-byte units
-                const int64_t src = static_cast<int64_t>(q) * a.nx + xa;
+                const int64_t src = static_cast<int64_t>(P * kq) * a.nx + xa;
                 const bool ok = xa - ox_in >= 0 && (xa - ox_in) * sizeof(S) + bytes <= SLOTIN * sizeof(S) &&
-                                src >= 0 && src * sizeof(S) + bytes <= static_cast<int64_t>(a.nx) * a.ns * sizeof(S) &&
+                                src >= 0 && (src + static_cast<int64_t>(nq - 1) * a.nx) * sizeof(S) + bytes <=
+                                                static_cast<int64_t>(a.nx) * a.ns * sizeof(S) &&
                                 bytes % 16 == 0 && (src * sizeof(S)) % 16 == 0 && ((xa - ox_in) * sizeof(S)) % 16 == 0;
                 if (!ok) {
                     atomicOr(a.status, kStatusBounds);
                     bytes = 0;
                 }
             }
-            mbar_arrive_expect_tx(bar, bytes);
-            if (bytes)
-                bulk_load(smem_addr(dst + (xa - ox_in)),
-                          static_cast<const S *>(a.in) + static_cast<int64_t>(q) * a.nx + xa, bytes, bar);
+            mbar_arrive_expect_tx(bar, bytes * static_cast<uint32_t>(nq));
+            if (bytes) {
+                const S *src = static_cast<const S *>(a.in) + static_cast<int64_t>(P * kq) * a.nx + xa;
+#pragma unroll
+                for (int j = 0; j < P; ++j)
+                    if (j < nq) bulk_load(smem_addr(dst0 + j * SLOTIN + (xa - ox_in)), src + static_cast<int64_t>(j) * a.nx, bytes, bar);
+            }
         } else {
+            const int q = kq;   // 3D: one plane per step
             if constexpr (CHK) {   // the box's x coordinate must be 16-byte aligned
                 if ((ox_in * static_cast<int>(sizeof(S))) % 16 != 0 || q < 0 || q >= a.ns) {
                     atomicOr(a.status, kStatusBounds);
@@ -629,12 +639,12 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                 }
             }
             mbar_arrive_expect_tx(bar, static_cast<uint32_t>(PWIN * G::PH * sizeof(S)));
-            tma_load_3d(smem_addr(dst), tmap, ox_in, oy, q, bar);
+            tma_load_3d(smem_addr(dst0), tmap, ox_in, oy, q, bar);
         }
     };
     if (tid == 0) {
-        const int qe = min(k0 + G::PF - 1, lmax);
-        for (int q = k0; q <= qe; ++q) issue(q);
+        const int qe = min(k0 + G::PFS - 1, smax);
+        for (int kq = k0; kq <= qe; ++kq) issue(kq);
     }
 
     float q[T][NQ][VY][4];
@@ -647,48 +657,50 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
 #pragma unroll
                 for (int v = 0; v < 4; ++v) q[s][j][vy][v] = 0.f;
 
-    int consumed_hi = k0 - 1;   // last input plane waited for by thread 0
+    int consumed_hi = k0 - 1;   // last input step waited for by thread 0
     bool aborted = false;
 
     // per-chunk state (a chunk is U steps; kb is a multiple of U)
     int kb = k0 - k0 % U;
-    int kb_mod = kb % DEPTH;
-    int lap = kb / DEPTH;
+    int kb_mod = kb % DS;       // step slot of step kb
+    int lap = kb / DS;
     uint32_t bar0 = 0, par = 0;
-    const S *inb = nullptr;     // own cell 0 in the input slot of plane kb
-    const S *inbp = nullptr;    // ROT: own cell 0 in the input slot of plane kb - QP
-    S *inslot = nullptr;        // input slot of plane kb
-    // shifting queue: FP32 ring slot of plane kb - lag(s) for level s = 1..T
+    const S *inb = nullptr;     // own cell 0 in the input slot of plane P*kb
+    const S *inbp = nullptr;    // ROT: own cell 0 in the input slot of plane P*kb - QP
+    S *inslot = nullptr;        // input slot of plane P*kb
+    // shifting queue (P = 1): FP32 ring slot of plane kb - lag(s) for level s = 1..T
     int rb[T + 1];
 #pragma unroll
     for (int s = 1; s <= T; ++s) rb[s] = cmod(kb - G::lag(s), QP);
 
-    // queue index of the plane level s computes at chunk step J
-    auto qnew = [](int s, int J) constexpr { return ROT ? cmod(J - G::lag(s), QP) : QP + J; };
-    // queue index of level s-1's plane p+e, read by level s at chunk step J (|e| <= R);
-    // level s-1 has computed plane p+R in this step (s = 1) or in the previous one (s >= 2)
-    auto qrd = [](int s, int J, int e) constexpr {
-        return ROT ? cmod(J - G::lag(s) + e, QP) : (s == 1 ? QP + J : QP + J - 1) - (R - e);
+    // queue index of plane P*k - lag(s) + j, which level s computes at chunk step J
+    auto qnew = [](int s, int J, int j) constexpr { return ROT ? cmod(P * J - G::lag(s) + j, QP) : QP + J; };
+    // queue index of level s-1's plane p+e, read by level s at chunk step J for its plane
+    // p = P*k - lag(s) + j (|e| <= R); level s-1 has computed plane p+R in this step (s = 1)
+    // or in an earlier one (s >= 2)
+    auto qrd = [](int s, int J, int j, int e) constexpr {
+        return ROT ? cmod(P * J - G::lag(s) + j + e, QP) : (s == 1 ? QP + J : QP + J - 1) - (R - e);
     };
-    // FP32 ring slot of level s's plane k - off - lag(s) at chunk step J (off = 0 or 1)
-    auto rslot = [&](int s, int J, int off) -> int {
+    // FP32 ring slot of level s's plane P*(k - off) - lag(s) + j at chunk step J (off = 0 or 1)
+    auto rslot = [&](int s, int J, int j, int off) -> int {
         if constexpr (ROT) {
-            return cmod(J - off - G::lag(s), QP);
+            return cmod(P * (J - off) - G::lag(s) + j, QP);
         } else {
-            int j = rb[s] + J - off;
-            j = j >= QP ? j - QP : j;
-            return j < 0 ? j + QP : j;
+            int jj = rb[s] + J - off;
+            jj = jj >= QP ? jj - QP : jj;
+            return jj < 0 ? jj + QP : jj;
         }
     };
 
-    // ---- one time level s of step k
-    auto level = [&](auto sc, auto Jc, auto CKc, int k) {
+    // ---- plane j of time level s at step k
+    auto level = [&](auto sc, auto Jc, auto jc, auto CKc, int k) {
         constexpr int s = decltype(sc)::value;
         constexpr int J = decltype(Jc)::value;
+        constexpr int j = decltype(jc)::value;
         constexpr bool CK = decltype(CKc)::value;
-        constexpr int jn = qnew(s, J);                 // own queue index of plane p
-        constexpr int jc = qrd(s, J, 0);               // level s-1's queue index of plane p
-        const int p = k - G::lag(s);
+        constexpr int jn = qnew(s, J, j);              // own queue index of plane p
+        constexpr int jcq = qrd(s, J, j, 0);           // level s-1's queue index of plane p
+        const int p = P * k - G::lag(s) + j;
         if constexpr (CK) {
             if (p < lo[s] || p > hi[s]) return;
             if (p > last) {   // beyond the end of the stream: repeat the last plane (clamp)
@@ -707,15 +719,15 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         const float *own32 = nullptr;
         if constexpr (s == 1) {
             if constexpr (ROT) {
-                constexpr int d = J - R;    // input slot of plane k-R relative to plane kb
+                constexpr int d = P * J - G::L1 + j;    // input slot of plane p relative to plane P*kb
                 own_in = d >= 0 ? inb + d * SLOTIN : inbp + (d + QP) * SLOTIN;
             } else {
-                int d = kb_mod + J - R;     // input slot of plane k-R
+                int d = kb_mod + J - R;     // input slot of plane k-R (P = 1)
                 d = d < 0 ? d + DEPTH : d;
                 own_in = ring_in + d * SLOTIN + toffin;
             }
         } else {
-            own32 = ring32(s - 1, rslot(s, J, 0)) + toff;
+            own32 = ring32(s - 1, rslot(s, J, j, 0)) + toff;
         }
         auto ld = [&](int row, int dx, float (&v)[4]) {
             if constexpr (s == 1) {
@@ -746,7 +758,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                 // radius 1 needs one cell on each side: the neighbouring lanes' own cells
                 // of the same plane; warp-edge and grid-edge lanes read shared memory
                 // (the neighbouring warp's cells, or the clamp frame)
-                const float(&c0)[VY][4] = q[s - 1][jc];
+                const float(&c0)[VY][4] = q[s - 1][jcq];
                 float l3 = __shfl_up_sync(0xffffffffu, c0[vy][3], 1);
                 float r0 = __shfl_down_sync(0xffffffffu, c0[vy][0], 1);
                 if (xedge) {
@@ -767,7 +779,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                     ld(vy, 4 * (m + 1), Rr[m]);
                 }
             }
-            const float(&ctr)[VY][4] = q[s - 1][jc];
+            const float(&ctr)[VY][4] = q[s - 1][jcq];
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 float acc = __fmul_rn(cf[0], ctr[vy][v]);
@@ -783,8 +795,8 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                         sv = (vy - i >= 0) ? ctr[cclamp(vy - i, 0, VY - 1)][v] : up[cclamp(i - vy - 1, 0, R - 1)][v];
                         nv = (vy + i < VY) ? ctr[cclamp(vy + i, 0, VY - 1)][v] : dn[cclamp(vy + i - VY, 0, R - 1)][v];
                     }
-                    const float bz = q[s - 1][qrd(s, J, -i)][vy][v];   // stream axis: S (2D) / B (3D)
-                    const float az = q[s - 1][qrd(s, J, i)][vy][v];    // N (2D) / A (3D)
+                    const float bz = q[s - 1][qrd(s, J, j, -i)][vy][v];   // stream axis: S (2D) / B (3D)
+                    const float az = q[s - 1][qrd(s, J, j, i)][vy][v];    // N (2D) / A (3D)
                     if constexpr (SH) {
                         // neighbours at distance i summed left to right (W, E, S, N[, B, A]),
                         // then one FMA with the shared coefficient
@@ -829,7 +841,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                     }
             }
         } else {
-            float *dst = ring32(s, rslot(s, J, 0)) + toff;
+            float *dst = ring32(s, rslot(s, J, j, 0)) + toff;
 #pragma unroll
             for (int vy = 0; vy < VY; ++vy) {
                 if (smem_ok(dst + vy * PW, 16)) Fmt<float>::store4(dst + vy * PW, res[vy]);
@@ -839,64 +851,76 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
             if constexpr (CK) {
                 if (p == 0) {   // top clamp: planes -r..-1 of this level equal plane 0
 #pragma unroll
-                    for (int j = 0; j < NQ; ++j)
+                    for (int jj = 0; jj < NQ; ++jj)
 #pragma unroll
                         for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
-                            for (int v = 0; v < 4; ++v) q[s][j][vy][v] = res[vy][v];
+                            for (int v = 0; v < 4; ++v) q[s][jj][vy][v] = res[vy][v];
                 }
             }
         }
     };
 
-    // ---- level 0 of step k: take plane k from the input ring
+    // ---- level 0 of step k: take planes P*k + j from the input ring
     auto level0 = [&](auto Jc, auto CKc, int k) {
         constexpr int J = decltype(Jc)::value;
         constexpr bool CK = decltype(CKc)::value;
-        const int p = k;
         if constexpr (CK) {
-            if (p < lo[0] || p > hi[0]) return;
-            if (p > last) {
-#pragma unroll
-                for (int vy = 0; vy < VY; ++vy)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) q[0][qnew(0, J)][vy][v] = q[0][ROT ? cmod(J - 1, QP) : QP + J - 1][vy][v];
+            if (P * k + P - 1 < lo[0] || P * k > hi[0]) return;
+        }
+        // the step's planes inside the grid were loaded together: one wait
+        if (!CK || P * k <= last) {
+            if (!mbar_wait_bounded(bar0 + 8 * J, par, a.timeout_ms)) {
+                *sflag = 1;
+                atomicOr(a.status, kStatusTimeout);
                 return;
             }
+            if (tid == 0) consumed_hi = k;
         }
-        if (!mbar_wait_bounded(bar0 + 8 * J, par, a.timeout_ms)) {
-            *sflag = 1;
-            atomicOr(a.status, kStatusTimeout);
-            return;
-        }
-        if (tid == 0) consumed_hi = p;
-        float v4[VY][4];
-#pragma unroll
-        for (int vy = 0; vy < VY; ++vy) {
-            if (smem_ok(inb + J * SLOTIN + vy * PWIN, 4 * sizeof(S))) Fmt<S>::load4(inb + J * SLOTIN + vy * PWIN, v4[vy]);
-            else v4[vy][0] = v4[vy][1] = v4[vy][2] = v4[vy][3] = 0.f;
-        }
-        if constexpr (D == 3 && VY > 1) clamp_rows(v4);
-#pragma unroll
-        for (int vy = 0; vy < VY; ++vy)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) q[0][qnew(0, J)][vy][v] = v4[vy][v];
-        if constexpr (CK) {
-            if (p == 0) {
-#pragma unroll
-                for (int j = 0; j < NQ; ++j)
+        SFor<0, P>::run([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            constexpr int jn = qnew(0, J, j);
+            const int p = P * k + j;
+            if constexpr (CK) {
+                if (p < lo[0] || p > hi[0]) return;
+                if (p > last) {
 #pragma unroll
                     for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
-                        for (int v = 0; v < 4; ++v) q[0][j][vy][v] = v4[vy][v];
+                        for (int v = 0; v < 4; ++v) q[0][jn][vy][v] = q[0][ROT ? cmod(jn - 1, QP) : QP + J - 1][vy][v];
+                    return;
+                }
             }
-        }
-        // the input slot is level 0's ring: clamp its out-of-grid frame now (read from step k+1 on)
-        if (gh_on) {
-            if constexpr (X4) ghost_fill_x4<sizeof(S)>(inslot + J * SLOTIN, gxin, PWIN, ox_in, a.nx, tid, NTHR);
-            else if constexpr (SAME) ghost_apply<sizeof(S)>(inslot + J * SLOTIN, gp32);
-            else ghost_apply<sizeof(S)>(inslot + J * SLOTIN, gpin);
-        }
+            const S *src = inb + (P * J + j) * SLOTIN;
+            float v4[VY][4];
+#pragma unroll
+            for (int vy = 0; vy < VY; ++vy) {
+                if (smem_ok(src + vy * PWIN, 4 * sizeof(S))) Fmt<S>::load4(src + vy * PWIN, v4[vy]);
+                else v4[vy][0] = v4[vy][1] = v4[vy][2] = v4[vy][3] = 0.f;
+            }
+            if constexpr (D == 3 && VY > 1) clamp_rows(v4);
+#pragma unroll
+            for (int vy = 0; vy < VY; ++vy)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) q[0][jn][vy][v] = v4[vy][v];
+            if constexpr (CK) {
+                if (p == 0) {
+#pragma unroll
+                    for (int jj = 0; jj < NQ; ++jj)
+#pragma unroll
+                        for (int vy = 0; vy < VY; ++vy)
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) q[0][jj][vy][v] = v4[vy][v];
+                }
+            }
+            // the input slot is level 0's ring: clamp its out-of-grid frame now (read from the
+            // next step on)
+            if (gh_on) {
+                if constexpr (X4) ghost_fill_x4<sizeof(S)>(inslot + (P * J + j) * SLOTIN, gxin, PWIN, ox_in, a.nx, tid, NTHR);
+                else if constexpr (SAME) ghost_apply<sizeof(S)>(inslot + (P * J + j) * SLOTIN, gp32);
+                else ghost_apply<sizeof(S)>(inslot + (P * J + j) * SLOTIN, gpin);
+            }
+        });
     };
 
     // ---- one step
@@ -908,31 +932,33 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         if constexpr (CK) {
             if (k < k0 || k > k1) return;
         }
-        // keep PF input planes in flight
+        // keep PFS steps of input in flight
         if (tid == 0) {
-            const int qn = k + G::PF;
-            if (qn <= lmax) {
+            const int kn = k + G::PFS;
+            if (kn <= smax) {
                 if (gh_on) fence_proxy_async_smem();
-                issue(qn);
+                issue(kn);
             }
         }
         // levels T..2 highest first, then level 0 (the input), then level 1 (reads the input ring)
         SFor<0, T - 1>::run([&](auto ic) {
             constexpr int s = T - decltype(ic)::value;
-            level(IC<s>{}, Jc, CKc, k);
+            SFor<0, P>::run([&](auto jc) { level(IC<s>{}, Jc, jc, CKc, k); });
         });
         level0(Jc, CKc, k);
-        level(IC<1>{}, Jc, CKc, k);
+        SFor<0, P>::run([&](auto jc) { level(IC<1>{}, Jc, jc, CKc, k); });
         // clamp frame of ring planes written in the previous step
         if (gh_on) {
             SFor<1, T>::run([&](auto sc) {
                 constexpr int s = decltype(sc)::value;
-                const int p = k - 1 - G::lag(s);
-                if (p >= lo[s] && p <= min(hi[s], last))
-                {
-                    if constexpr (X4) ghost_fill_x4<4>(ring32(s, rslot(s, J, 1)), gx32, PW, ox, a.nx, tid, NTHR);
-                    else ghost_apply<4>(ring32(s, rslot(s, J, 1)), gp32);
-                }
+                SFor<0, P>::run([&](auto jc) {
+                    constexpr int j = decltype(jc)::value;
+                    const int p = P * (k - 1) - G::lag(s) + j;
+                    if (p >= lo[s] && p <= min(hi[s], last)) {
+                        if constexpr (X4) ghost_fill_x4<4>(ring32(s, rslot(s, J, j, 1)), gx32, PW, ox, a.nx, tid, NTHR);
+                        else ghost_apply<4>(ring32(s, rslot(s, J, j, 1)), gp32);
+                    }
+                });
             });
         }
         __syncthreads();
@@ -942,9 +968,9 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     for (; kb <= k1 && !aborted; kb += U) {
         par = static_cast<uint32_t>((lap - lap0) & 1);
         bar0 = smem_addr(bars + kb_mod);
-        inslot = ring_in + kb_mod * SLOTIN;
+        inslot = ring_in + kb_mod * P * SLOTIN;
         inb = inslot + toffin;
-        if constexpr (ROT) inbp = ring_in + (kb_mod == 0 ? DEPTH - QP : kb_mod - QP) * SLOTIN + toffin;
+        if constexpr (ROT) inbp = ring_in + (kb_mod == 0 ? DEPTH - QP : P * kb_mod - QP) * SLOTIN + toffin;
         if (kb >= kA && kb + U - 1 <= kB) {
             SFor<0, U>::run([&](auto Jc) { step(Jc, std::false_type{}); });
         } else {
@@ -955,16 +981,16 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
 #pragma unroll
             for (int s = 0; s < T; ++s)
 #pragma unroll
-                for (int j = 0; j < QP; ++j)
+                for (int jj = 0; jj < QP; ++jj)
 #pragma unroll
                     for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
-                        for (int v = 0; v < 4; ++v) q[s][j][vy][v] = q[s][j + U][vy][v];
+                        for (int v = 0; v < 4; ++v) q[s][jj][vy][v] = q[s][jj + U][vy][v];
 #pragma unroll
             for (int s = 1; s <= T; ++s) rb[s] = rb[s] + U >= QP ? rb[s] + U - QP : rb[s] + U;
         }
         kb_mod += U;
-        if (kb_mod == DEPTH) {
+        if (kb_mod == DS) {
             kb_mod = 0;
             ++lap;
         }
@@ -972,15 +998,14 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
 
     if (aborted && tid == 0) {
         // let the copies still in flight land before the block's shared memory is released
-        for (int qq = consumed_hi + 1; qq <= issued_hi; ++qq) {
-            if (qq == a.fault_plane) continue;
-            mbar_wait_bounded(smem_addr(bars + qq % DEPTH), static_cast<uint32_t>((qq / DEPTH - lap0) & 1),
-                              a.timeout_ms);
+        for (int kq = consumed_hi + 1; kq <= issued_hi; ++kq) {
+            if (a.fault_plane >= P * kq && a.fault_plane < P * kq + P) continue;
+            mbar_wait_bounded(smem_addr(bars + kq % DS), static_cast<uint32_t>((kq / DS - lap0) & 1), a.timeout_ms);
         }
     }
     __syncthreads();
     if (tid == 0)
-        for (int i = 0; i < DEPTH; ++i) mbar_inval(smem_addr(bars + i));
+        for (int i = 0; i < DS; ++i) mbar_inval(smem_addr(bars + i));
     __syncthreads();
     return !aborted;
 }
@@ -991,7 +1016,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
 // column b mod (ntx*nty), planes [j*seg, (j+1)*seg) with j = b / (ntx*nty),
 // so blocks running together cover neighbouring tiles of the same planes and
 // share their overlapping halo reads in L2.
-template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH, bool CHK>
+template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH, bool CHK, int P>
 __device__ __forceinline__ bool sweep_block(const CUtensorMap *tmap, const SweepArgs &a, int b, unsigned char *smem)
 {
     const int cols = a.ntx * a.nty;
@@ -1010,7 +1035,7 @@ __device__ __forceinline__ bool sweep_block(const CUtensorMap *tmap, const Sweep
         const int col = static_cast<int>(w / a.ns);
         const int z0 = static_cast<int>(w - static_cast<int64_t>(col) * a.ns);
         const int z1 = static_cast<int>(min(static_cast<int64_t>(a.ns), z0 + (we - w)));
-        ok = sweep_tile<D, R, T, VY, S, TX, TY, SH, CHK>(tmap, a, col, z0, z1, smem);
+        ok = sweep_tile<D, R, T, VY, S, TX, TY, SH, CHK, P>(tmap, a, col, z0, z1, smem);
         w += z1 - z0;
     }
     return ok;
@@ -1018,12 +1043,12 @@ __device__ __forceinline__ bool sweep_block(const CUtensorMap *tmap, const Sweep
 
 // ------------------------------------------------------------------ kernels
 // One pass over the grid: block b sweeps its planes of the tile columns (sweep_block).
-template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH, bool CHK>
+template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH, bool CHK, int P>
 __global__ void __launch_bounds__(TX *TY)
     sweep_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ SweepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    sweep_block<D, R, T, VY, S, TX, TY, SH, CHK>(&tmap, a, static_cast<int>(blockIdx.x), smem);
+    sweep_block<D, R, T, VY, S, TX, TY, SH, CHK, P>(&tmap, a, static_cast<int>(blockIdx.x), smem);
 }
 
 // Persistent sweep of many grids of one kernel class, all passes, from a device tile
@@ -1061,7 +1086,7 @@ __device__ __forceinline__ void fence_proxy_async_global()
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH, bool CHK>
+template <int D, int R, int T, int VY, typename S, int TX, int TY, bool SH, bool CHK, int P>
 __global__ void __launch_bounds__(TX *TY)
     sweep_persistent(const __grid_constant__ BatchArgs B)
 {
@@ -1107,7 +1132,7 @@ __global__ void __launch_bounds__(TX *TY)
         __syncthreads();
         if (!s_ok) break;
         const SweepArgs a = B.args[task];
-        const bool done = sweep_block<D, R, T, VY, S, TX, TY, SH, CHK>(D == 3 ? B.maps + task : nullptr, a, q - tk.first, smem);
+        const bool done = sweep_block<D, R, T, VY, S, TX, TY, SH, CHK, P>(D == 3 ? B.maps + task : nullptr, a, q - tk.first, smem);
         __syncthreads();
         if (tid == 0 && task != B.fault_task) {
             __threadfence();

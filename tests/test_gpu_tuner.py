@@ -143,10 +143,12 @@ def test_tuning_cache_file_is_shared_between_handles(tmp_path, monkeypatch):
     base = a.default_schedule((ny, nx))
     chosen, _ = st.stencil_tune(a.handle, nx, ny, 1, st.STENCIL_F32, st.TUNE_ANALYTIC, store=True)
     line = path.read_text().strip().splitlines()[-1].split()
-    assert line[0] == "v1" and [int(v) for v in line[2:9]] == [dim, r, 0, 0, nx, ny, 1]
+    assert line[0] == "v2" and [int(v) for v in line[2:9]] == [dim, r, 0, 0, nx, ny, 1]
+    assert int(line[-1]) == chosen.planes_per_step
     b = st.Stencil(dim, r, c)
     got = b.default_schedule((ny, nx))
-    assert (got.t, got.seg, got.kernel) == (chosen.t, chosen.seg, chosen.kernel)
+    assert (got.t, got.seg, got.kernel, got.planes_per_step) == (chosen.t, chosen.seg, chosen.kernel,
+                                                                 chosen.planes_per_step)
     f = gen.workload_grid(dim, nx, ny)
     out = b.run(torch.from_numpy(f).cuda(), 7).cpu().numpy()
     assert np.array_equal(out, oracle.sweep_f32(f, dim, r, c, 7))
