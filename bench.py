@@ -55,7 +55,10 @@ def crop_input(side: int) -> np.ndarray:
     return out
 
 
-def peaks():
+def peaks(measure: bool = True):
+    """Roofline denominators: HBM from MEASURED_PEAKS.json (the pool's copy measurement), FP32
+    from the library's FMA-throughput kernel on this device (nominal unit count x clock if not
+    measured)."""
     p = {"hbm_gbs": FALLBACK_HBM_GBS, "hbm_src": "fallback"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -65,6 +68,14 @@ def peaks():
             p = {"hbm_gbs": float(m["hbm_gbs"]), "hbm_src": "measured"}
     from paper_2002_05983_gb300 import metrics
     p["fp32_flops"] = metrics.FP32_PEAK_NOMINAL
+    p["fp32_src"] = "nominal: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+    if measure:
+        import paper_2002_05983_gb300 as st
+        m = st.stencil_measure_peaks()
+        p["fp32_flops"] = m.fp32_flops
+        p["fp32_src"] = (f"measured: FMA-throughput kernel, {m.sms} SMs "
+                         f"(nominal {metrics.FP32_PEAK_NOMINAL / 1e12:.2f} TFLOP/s)")
+        p["copy_gbs_library"] = m.copy_bytes_per_s / 1e9
     return p
 
 
@@ -496,6 +507,140 @@ def tune_main(args):
     return 0
 
 
+def _event_time(fn, reps, stream):
+    """Best CUDA-event time of fn() on `stream` over reps runs (after one warm-up run)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return best
+
+
+def measure_3d(pk, stream):
+    """3D 512^3 FP32, 200 iterations, radius 1..4 at the library's default schedule (seeded
+    uniform + Gaussian-bump input); per radius GCell/s and the fraction of R(t)."""
+    import torch
+    import paper_2002_05983_gb300 as st
+    from paper_2002_05983_gb300 import metrics
+    n, iters = 512, 200
+    x = torch.from_numpy(gen.workload_grid(3, n, n, n)).cuda()
+    out = torch.empty_like(x)
+    rows = []
+    for r in RADII:
+        s = st.Stencil(3, r, gen.coefficients(3, r))
+        d = s.default_schedule((n, n, n))
+        sec = _event_time(lambda: s.run(x, iters, out=out), 3, stream)
+        g = x.numel() * iters / sec / 1e9
+        roof = metrics.roofline_cells(3, r, d.t, 4, pk["fp32_flops"], pk["hbm_gbs"] * 1e9) / 1e9
+        rows.append({"r": r, "t": d.t, "rows_per_thread": d.rows_per_thread, "gcells": round(g, 2),
+                     "gflops": round(g * metrics.flop_per_cell(3, r), 1), "roofline_gcells": round(roof, 1),
+                     "roofline_frac": round(g / roof, 4),
+                     "bound": metrics.roofline_bound(3, r, d.t, 4, pk["fp32_flops"], pk["hbm_gbs"] * 1e9),
+                     "ms": round(sec * 1e3, 2)})
+        s.close()
+    assert st.stencil_get_device_status() == 0
+    return {"grid": [n, n, n], "iters": iters, "input": "uniform [0,1) seed 0 + Gaussian bump sigma 16",
+            "radii": rows}
+
+
+def measure_precision(pk, stream):
+    """Radius 4 on 768^3 (3D) and 32768^2 (2D), 500 iterations, FP32 vs BF16 vs FP16 storage at the
+    default schedules: speed-up over FP32 (timing grids: torch.rand on the device, values do not
+    change the speed), and the error after 500 steps against the FP64 oracle on the seeded
+    128^3 / 2048^2 instances."""
+    import torch
+    import oracle
+    import paper_2002_05983_gb300 as st
+    from paper_2002_05983_gb300 import metrics
+    iters, r = 500, 4
+    out = {}
+    dts = (("f32", torch.float32, 4), ("bf16", torch.bfloat16, 2), ("f16", torch.float16, 2))
+    for dim, n, small in ((3, 768, 128), (2, 32768, 2048)):
+        s = st.Stencil(dim, r, gen.coefficients(dim, r))
+        key = f"{dim}d_{n}"
+        res = {}
+        g = torch.Generator(device="cuda")
+        g.manual_seed(1)
+        for name, dt, es in dts:
+            x = torch.rand((n,) * dim, device="cuda", generator=g).to(dt)
+            y = torch.empty_like(x)
+            d = s.default_schedule((n,) * dim, st.dtype_code(x))
+            sec = _event_time(lambda: s.run(x, iters, out=y), 1, stream)
+            gc = x.numel() * iters / sec / 1e9
+            roof = metrics.roofline_cells(dim, r, d.t, es, pk["fp32_flops"], pk["hbm_gbs"] * 1e9) / 1e9
+            res[name] = {"t": d.t, "planes_per_step": d.planes_per_step, "gcells": round(gc, 2),
+                         "roofline_frac": round(gc / roof, 4)}
+            del x, y
+            torch.cuda.empty_cache()
+        for name in ("bf16", "f16"):
+            res[name]["speedup_vs_f32"] = round(res[name]["gcells"] / res["f32"]["gcells"], 3)
+        f = gen.workload_grid(dim, *((small,) * dim))
+        c = gen.coefficients(dim, r)
+        w64 = oracle.sweep_f64(f.astype(np.float64), dim, r, c.astype(np.float64), iters)
+        for name, dt, _ in dts:
+            xs = torch.from_numpy(f).to(dt)
+            got = s.run(xs.cuda(), iters).float().cpu().numpy().astype(np.float64)
+            res[name]["accuracy"] = {"grid": [small] * dim, "iters": iters,
+                                     "max_abs_vs_fp64": float(np.max(np.abs(got - w64))),
+                                     "rel_l2_vs_fp64": float(np.linalg.norm(got - w64) / np.linalg.norm(w64))}
+        out[key] = res
+        s.close()
+    assert st.stencil_get_device_status() == 0
+    return out
+
+
+def measure_batched(stream):
+    """The 96-grid mixed batch (64 2D sides 512-8192, 32 3D sides 64-384, radius 1-4, FP32/BF16,
+    100 iterations each; rows rounded down to 8 cells) as one stencil_run_batched call against
+    the same grids swept one stencil_run after another."""
+    import torch
+    import paper_2002_05983_gb300 as st
+    iters = 100
+    items = gen.batch_list()
+    stencils, bufs, batch = {}, [], []
+    g = torch.Generator(device="cuda")
+    g.manual_seed(100)
+    for it in items:
+        it["nx"] -= it["nx"] % 8
+        key = (it["dim"], it["r"])
+        if key not in stencils:
+            stencils[key] = st.Stencil(it["dim"], it["r"], gen.coefficients(*key))
+        shape = (it["ny"], it["nx"]) if it["dim"] == 2 else (it["nz"], it["ny"], it["nx"])
+        dt = torch.bfloat16 if it["dtype"] == "bf16" else torch.float32
+        x = torch.rand(shape, device="cuda", generator=g).to(dt)
+        y = torch.empty_like(x)
+        bufs.append((x, y))
+        batch.append((stencils[key].handle, x.data_ptr(), y.data_ptr(), it["nx"], it["ny"], it["nz"], iters,
+                      st.dtype_code(x)))
+    sp = stream.cuda_stream
+    cells = sum(b[3] * b[4] * b[5] for b in batch) * iters
+
+    def singles():
+        for h, xp, yp, nx, ny, nz, it_, code in batch:
+            st.stencil_run(h, xp, yp, nx, ny, nz, it_, code, sp)
+
+    t_single = _event_time(singles, 2, stream)
+    ref = [y.clone() for _, y in bufs]
+    t_batch = _event_time(lambda: st.stencil_run_batched(batch, sp), 3, stream)
+    assert st.stencil_get_device_status() == 0
+    same = sum(int(torch.equal(y, r)) for (_, y), r in zip(bufs, ref))
+    res = {"grids": len(batch), "grids_2d": sum(1 for it in items if it["dim"] == 2), "iters": iters,
+           "cell_updates": cells, "seconds_individual": round(t_single, 4), "seconds_batched": round(t_batch, 4),
+           "gcells_individual": round(cells / t_single / 1e9, 1), "gcells_batched": round(cells / t_batch / 1e9, 1),
+           "speedup_vs_individual": round(t_single / t_batch, 3),
+           "grids_bit_identical_to_individual": f"{same}/{len(batch)}"}
+    for s in stencils.values():
+        s.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -503,6 +648,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 3D, 16-bit storage and batch measurements that follow the headline")
     ap.add_argument("--suite", choices=["sweep2d", "sweep3d", "precision", "batch", "shared"], default=None,
                     help="other workloads: t sweeps, 16-bit storage, 96-grid batch, shared coefficients (JSON lines)")
     ap.add_argument("--radii", default="1,2,3,4",
@@ -568,6 +715,7 @@ def main():
                 f"{src.numel() * 4 / c0.elapsed_time(c1) / 1e6:.1f} GB/s")
 
     copy_bandwidth("before the sweeps")
+    pk = peaks()
     stencils = {r: st.Stencil(2, r, gen.coefficients(2, r)) for r in RADII}
     scheds = {r: stencils[r].default_schedule((NY, NX)) for r in RADII}
     stream = torch.cuda.current_stream()
@@ -627,7 +775,6 @@ def main():
            "d2h_bytes_per_step": host_out.numel() * 4 * len(RADII)}
 
     # ---- roofline of the dominant kernel (the radius with the longest time)
-    pk = peaks()
     rows = []
     launches = 0
     for r in RADII:
@@ -637,7 +784,7 @@ def main():
         sec = per_r[r]
         g = NX * NY * ITERS / sec / 1e9
         roof = metrics.roofline_cells(2, r, t, 4, pk["fp32_flops"], pk["hbm_gbs"] * 1e9) / 1e9
-        rows.append({"r": r, "t": t, "threads_x": scheds[r].threads_x, "gcells": round(g, 2),
+        rows.append({"r": r, "t": t, "planes_per_step": scheds[r].planes_per_step, "gcells": round(g, 2),
                      "gflops": round(g * metrics.flop_per_cell(2, r), 1),
                      "roofline_gcells": round(roof, 1), "roofline_frac": round(g / roof, 4),
                      "bound": metrics.roofline_bound(2, r, t, 4, pk["fp32_flops"], pk["hbm_gbs"] * 1e9),
@@ -652,8 +799,7 @@ def main():
     else:
         ach = NX * NY * dom["t"] * metrics.flop_per_cell(2, dom["r"]) / launch_s / 1e12
         roofline = {"bound": "alu", "achieved": round(ach, 2), "peak": round(pk["fp32_flops"] / 1e12, 2),
-                    "unit": "TFLOP/s",
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (nominal)"}
+                    "unit": "TFLOP/s", "peak_source": pk["fp32_src"]}
     roofline["frac"] = round(roofline["achieved"] / roofline["peak"], 4)
     roofline["kernel"] = f"sweep_kernel<2D, r={dom['r']}, t={dom['t']}, fp32>"
     roofline["traffic"] = traffic_for(2, dom["r"], dom["t"])
@@ -668,7 +814,17 @@ def main():
                        "l2": "inputs larger than L2 (1 GiB grid), no flush",
                        "parallelism": f"replicas x{world}"},
             "gflops": round(flops_step * args.steps * world / elapsed / 1e9, 1),
-            "per_radius": rows, "roofline": roofline, "e2e": e2e, "gpu_launches": launches}
+            "per_radius": rows, "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
+            "peaks": {"fp32_tflops": round(pk["fp32_flops"] / 1e12, 2), "fp32_source": pk["fp32_src"],
+                      "hbm_gbs": pk["hbm_gbs"], "hbm_source": pk["hbm_src"] + " (MEASURED_PEAKS.json)",
+                      "copy_gbs_library_kernel": round(pk.get("copy_gbs_library", 0.0), 1)}}
+    # ---- the other workloads (outside the timed region above): 3D, 16-bit storage, batch
+    if not args.no_extra:
+        t_extra = time.time()
+        line["per_radius_3d"] = measure_3d(pk, stream)
+        line["precision"] = measure_precision(pk, stream)
+        line["batched"] = measure_batched(stream)
+        log(f"rank {rank}: 3D, precision and batch measurements took {time.time() - t_extra:.1f}s")
     clk = clk.summary()
     if clk:
         line["clocks"] = clk

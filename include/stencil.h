@@ -270,7 +270,8 @@ int stencil_run_batched(const stencil_batch_item *items, int n, void *stream);
 /* Synchronise `stream`, then read and return the sticky device status of the
  * current device: STENCIL_OK, STENCIL_ERR_TIMEOUT when a kernel gave up a
  * bounded wait (it then stopped early and its output is not valid), or
- * STENCIL_ERR_BOUNDS when a bounds-checked kernel skipped an access.
+ * STENCIL_ERR_BOUNDS when a bounds-checked kernel skipped an access.  The
+ * status covers every entry point, stencil_run_noalloc included.
  * `clear` != 0 resets the status to OK afterwards. */
 int stencil_get_device_status(void *stream, int clear);
 
@@ -296,28 +297,46 @@ int stencil_set_fault_injection(stencil_handle h, int plane, int timeout_ms);
 int stencil_set_checked(stencil_handle h, int on);
 
 /* stencil_run without any device memory allocation, for callers that cannot
- * allocate: code that runs while a CUDA graph is being captured (where
- * cudaMalloc is not allowed), code inside an allocator's out-of-memory path,
- * or processes whose device memory is handed out by an external budget.
- * The paper has no counterpart; this is a library-level variant.
+ * allocate: code inside an allocator's out-of-memory path (where a cudaMalloc
+ * would recurse or fail), or processes whose device memory is handed out by an
+ * external budget that the library must not draw on.  The paper has no
+ * counterpart; this is a library-level variant.
  *  - The second grid of the ping-pong between passes is a 16 MiB array
- *    compiled into the library (every GPU that loads the library holds it
- *    until the process exits), so nx*ny*nz*sizeof(dtype) must be at most
- *    16 MiB (4M FP32 cells, 8M BF16/FP16 cells); larger grids are rejected
- *    with STENCIL_ERR_INVALID_ARG before any device work.
+ *    compiled into the library (every GPU that loads the library holds it until
+ *    the process exits), so nx*ny*nz*sizeof(dtype) must be at most 16 MiB (4M
+ *    FP32 cells, 8M BF16/FP16 cells); larger grids are rejected with
+ *    STENCIL_ERR_INVALID_ARG before any device work.
  *  - The first call on a device looks up the array's device address and the
  *    device attributes; make that first call before any stream capture.
  *  - All calls on a device share the array, which keeps the last call's
  *    contents: calls whose work overlaps on the GPU (different streams, or
  *    different handles at the same time) race and give wrong results.
- *  - The schedule is the one stencil_run would pick (no tuned schedules are
- *    consulted); results equal stencil_run's bit for bit.
- *  - A kernel whose bounded wait expires records it in a device word of this
- *    entry point that each call resets; it is not reported by
- *    stencil_get_device_status.
+ *  - The schedule is the library's default rule (stencil_default_schedule
+ *    without picks stored by stencil_tune or read from the tuning-cache file);
+ *    every FP32 schedule gives the same bits, so results equal stencil_run's.
+ *  - A kernel whose bounded wait expires records it in a status word of this
+ *    entry point (sticky, like the library's main status word);
+ *    stencil_get_device_status reports it as STENCIL_ERR_TIMEOUT and clears
+ *    it with clear != 0.
  * Arguments and other errors as stencil_run. */
 int stencil_run_noalloc(stencil_handle h, const void *in, void *out, int64_t nx, int64_t ny,
                         int64_t nz, int iters, int dtype, void *stream);
+
+/* Measured peaks of the current device, the denominators of the roofline
+ * R(t) = min(P_fp32 / F, BW * t / (2 s)) (Table IV/V's roofline ratio, re-done
+ * for the GPU): fp32_flops is the FP32 fused multiply-add throughput of the
+ * CUDA cores (independent FMA chains in every thread, 2 FLOP per FMA, CUDA-event
+ * timed), copy_bytes_per_s the bytes read plus written per second by a 16-byte
+ * copy kernel over 1 GiB buffers (above the L2 size).  sms and sm_clock_khz are
+ * the device attributes.  Allocates two 1 GiB buffers for the call (cudaMalloc)
+ * and synchronises `stream`.  Errors: INVALID_ARG, OOM, CUDA. */
+typedef struct {
+    double fp32_flops;
+    double copy_bytes_per_s;
+    int sms;
+    int sm_clock_khz;
+} stencil_peaks;
+int stencil_measure_peaks(void *stream, stencil_peaks *out);
 
 /* cudaError_t of the last failed CUDA call on this host thread (0 if none). */
 int stencil_last_cuda_error(void);

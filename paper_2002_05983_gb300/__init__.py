@@ -34,7 +34,8 @@ EXPORTS = ("stencil_create", "stencil_create_shared", "stencil_destroy", "stenci
            "stencil_set_fault_injection", "stencil_set_checked", "stencil_run_noalloc", "stencil_run_batched", "stencil_tune",
            "stencil_schedule_features", "stencil_model_create", "stencil_model_destroy",
            "stencil_model_train", "stencil_model_predict", "stencil_model_normalization",
-           "stencil_model_params", "stencil_model_grad", "stencil_last_cuda_error", "stencil_strerror")
+           "stencil_model_params", "stencil_model_grad", "stencil_measure_peaks", "stencil_last_cuda_error",
+           "stencil_strerror")
 
 NFEAT = 14
 TUNE_ANALYTIC, TUNE_EXHAUSTIVE, TUNE_MODEL = 0, 1, 2
@@ -61,6 +62,12 @@ class BatchItem(ctypes.Structure):
     """stencil_batch_item."""
     _fields_ = [("h", ctypes.c_void_p), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("nx", ctypes.c_int64),
                 ("ny", ctypes.c_int64), ("nz", ctypes.c_int64), ("iters", ctypes.c_int), ("dtype", ctypes.c_int)]
+
+
+class Peaks(ctypes.Structure):
+    """stencil_peaks: measured FP32 FMA throughput and copy bandwidth of the device."""
+    _fields_ = [("fp32_flops", ctypes.c_double), ("copy_bytes_per_s", ctypes.c_double), ("sms", ctypes.c_int),
+                ("sm_clock_khz", ctypes.c_int)]
 
 
 class Timing(ctypes.Structure):
@@ -107,6 +114,7 @@ def _lib():
                 lib.stencil_model_normalization.argtypes = [vp, fp, fp, ctypes.c_float, ctypes.c_float]
                 lib.stencil_model_params.argtypes = [vp, fp, i32, i32]
                 lib.stencil_model_grad.argtypes = [vp, fp, fp, i32, fp, fp]
+                lib.stencil_measure_peaks.argtypes = [vp, ctypes.POINTER(Peaks)]
                 lib.stencil_last_cuda_error.argtypes = []
                 lib.stencil_strerror.argtypes = [i32]
                 lib.stencil_strerror.restype = ctypes.c_char_p
@@ -290,6 +298,13 @@ def stencil_model_grad(m, X, y):
     loss = np.zeros(1, np.float32)
     _check(_lib().stencil_model_grad(m, _fptr(X), _fptr(y), len(y), _fptr(loss), _fptr(g)), "stencil_model_grad")
     return float(loss[0]), g
+
+
+def stencil_measure_peaks(stream=None) -> Peaks:
+    """Measured FP32 FMA throughput (FLOP/s) and copy bandwidth (bytes/s) of the current device."""
+    p = Peaks()
+    _check(_lib().stencil_measure_peaks(stream, ctypes.byref(p)), "stencil_measure_peaks")
+    return p
 
 
 def stencil_last_cuda_error() -> int:

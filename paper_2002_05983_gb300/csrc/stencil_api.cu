@@ -885,12 +885,15 @@ int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cuda
 
 // ------------------------------------------------------------------------
 // Scratch for stencil_run_noalloc.  Callers that must not allocate device
-// memory (code running while a CUDA graph is captured, inside an allocator's
-// out-of-memory path, or under an external memory budget) still need the
-// second grid of the ping-pong between passes; it lives in this file-scope
-// array instead, which every GPU that loads the library holds until exit.
-// In host code the array's name is only a stand-in: its device address is
-// fetched once per device with cudaGetSymbolAddress below.
+// memory (code inside an allocator's out-of-memory path, or processes whose
+// device memory is handed out by an external budget) still need the second
+// grid of the ping-pong between passes; it lives in this file-scope array
+// instead, which every GPU that loads the library holds until exit.  In host
+// code the array's name is only a stand-in: its device address is fetched
+// once per device with cudaGetSymbolAddress below.  The status word next to it
+// is where kernels launched by stencil_run_noalloc record an expired bounded
+// wait; it is zero when the module loads, sticky like the main status word, and
+// read and cleared by stencil_get_device_status.
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;   // 16 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 static __device__ __align__(256) unsigned g_noalloc_status[64];
@@ -903,6 +906,14 @@ struct NoAllocDev {
 };
 std::mutex g_noalloc_mu;
 NoAllocDev g_noalloc[64];
+
+// Status word of stencil_run_noalloc on device `dev`, or null if no call has set it up.
+unsigned *noalloc_status_word(int dev)
+{
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    return g_noalloc[dev].ready ? g_noalloc[dev].status : nullptr;
+}
 
 // Set-up of the current device (first call on that device): symbol
 // addresses and the attributes the planner needs.  Allocates nothing.
@@ -1034,11 +1045,20 @@ int stencil_get_device_status(void *stream, int clear)
     DevInfo *dev = nullptr;
     int rc = device_info(&dev);
     if (rc) return rc;
+    int devno = 0;
+    CK(cudaGetDevice(&devno));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CK(cudaStreamSynchronize(st));
     unsigned word = 0;
     CK(cudaMemcpy(&word, dev->status, sizeof(word), cudaMemcpyDeviceToHost));
     if (clear) CK(cudaMemset(dev->status, 0, sizeof(unsigned)));
+    // the word of stencil_run_noalloc's kernels on this device, once that entry point ran here
+    if (unsigned *nw = noalloc_status_word(devno)) {
+        unsigned w2 = 0;
+        CK(cudaMemcpy(&w2, nw, sizeof(w2), cudaMemcpyDeviceToHost));
+        word |= w2;
+        if (clear) CK(cudaMemset(nw, 0, sizeof(unsigned)));
+    }
     if (word & stn::kStatusTimeout) return STENCIL_ERR_TIMEOUT;
     if (word & stn::kStatusBounds) return STENCIL_ERR_BOUNDS;
     return STENCIL_OK;
@@ -1076,9 +1096,8 @@ int stencil_run_noalloc(stencil_handle h, const void *in, void *out, int64_t nx,
     rc = noalloc_device(&nd);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // the status word must start at zero for this call; the scratch grid needs
-    // no clearing (every pass writes all of it before the next pass reads it)
-    CK(cudaMemsetAsync(nd->status, 0, sizeof(unsigned), st));
+    // the scratch grid needs no clearing: every pass writes all of it before the next
+    // pass reads it.  The status word is sticky (stencil_get_device_status clears it).
     if (iters == 0) {
         CK(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st));
         return STENCIL_OK;
@@ -1087,7 +1106,7 @@ int stencil_run_noalloc(stencil_handle h, const void *in, void *out, int64_t nx,
     dev.sms = nd->sms;
     dev.max_smem = nd->max_smem;
     dev.status = nd->status;
-    stencil_schedule s;
+    stencil_schedule s;   // the library's rule only: no tuned or cached picks
     default_schedule(h, nx, ny, nz, dtype, &s);
     const bool aligned = (reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16 == 0;
     const bool streamable = s.kernel == STENCIL_KERNEL_STREAM && aligned;
