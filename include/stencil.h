@@ -248,19 +248,23 @@ typedef struct {
 } stencil_batch_item;
 
 /* Sweep many independent grids of mixed dimension, radius and storage type
- * together.  Grids are grouped by kernel class (dim, radius, dtype, temporal
- * degree, rows per thread); each class runs as ONE persistent launch whose
- * blocks take tiles from a device-side queue ordered pass by pass over all
- * grids of the class, largest grids first; a tile of pass p of a grid starts
- * only when all tiles of its pass p-1 are done (bounded wait: on expiry the
- * device status is set, see stencil_get_device_status).  The class launches
- * are captured once into a CUDA graph, cached for this exact item list (same
- * pointers, sizes, handles) and replayed on `stream` by later calls.  Each
- * grid uses its handle's tuned or default temporal degree, lowered to the
- * largest compiled degree that divides `iters` (so every pass of a grid has
- * the same degree); results equal stencil_run_ex with that degree bit for
- * bit.  The batch owns one scratch grid per item (allocated on the first call
- * for an item list, before capture) and keeps up to four cached lists.
+ * together (not in the paper; a serving-style batch of the paper's sweep).
+ * Each grid runs exactly the passes stencil_run would: iters / t passes of its
+ * handle's tuned or default degree t, then one remainder pass of degree
+ * iters mod t, so results equal stencil_run's bit for bit.  Passes are grouped
+ * by kernel class (dim, radius, dtype, temporal degree, rows per thread or per
+ * step); each class runs as ONE persistent launch whose blocks take tiles from
+ * a device-side queue ordered pass by pass over all grids of the class,
+ * largest grids first; a tile of pass p of a grid starts only when all tiles
+ * of its pass p-1 are done (bounded wait: on expiry the device status is set,
+ * see stencil_get_device_status).  All class launches of the full passes are
+ * captured as parallel branches of one CUDA graph, so the classes run side by
+ * side and one class's last wave overlaps the others' work; the remainder
+ * passes follow as a second set of parallel branches once every full pass is
+ * done.  The graph is cached for this exact item list (same pointers, sizes,
+ * handles, schedules) and replayed on `stream` by later calls.  The batch owns
+ * one scratch grid per item (allocated on the first call for an item list,
+ * before capture) and keeps up to four cached lists.
  * Every grid must allow the streaming kernel (rows 16-byte aligned: nx % 4
  * FP32, nx % 8 16-bit; 16-byte aligned pointers), else STENCIL_ERR_UNSUPPORTED.
  * Items may share a handle; `in` of one item must not overlap any `out`.
@@ -276,13 +280,14 @@ int stencil_run_batched(const stencil_batch_item *items, int n, void *stream);
 int stencil_get_device_status(void *stream, int clear);
 
 /* Test hook for failure detection: while `plane` >= 0, streaming kernels on
- * this handle never issue the copy of that input plane, so the wait for it
- * expires after `timeout_ms` milliseconds (1..10000), the kernel records
- * STENCIL_ERR_TIMEOUT in the device status and returns without hanging.
- * plane < 0 restores normal operation (and the default 2000 ms limit).
- * In stencil_run_batched the same setting makes pass number `plane` of the
- * grids swept with this handle never report completion, so the bounded waits
- * of their next pass expire. */
+ * this handle never issue the copy of that input plane (with two rows per
+ * step: of the step holding it), so the wait for it expires after `timeout_ms`
+ * milliseconds (1..10000), the kernel records STENCIL_ERR_TIMEOUT in the
+ * device status and returns without hanging.  plane < 0 restores normal
+ * operation (and the default 2000 ms limit).  In stencil_run_batched the same
+ * setting makes full pass number `plane` of the grids swept with this handle
+ * never report completion, so the bounded waits of their next full pass
+ * expire. */
 int stencil_set_fault_injection(stencil_handle h, int plane, int timeout_ms);
 
 /* Memory-checker substitute: with on = 1, streaming sweeps on this handle use

@@ -693,6 +693,7 @@ int candidates(const stencil_plan *h, int64_t ny, int64_t nz, int dtype, stencil
 // Batched persistent sweeps: plans, device task tables and cached CUDA graphs.
 struct BatchClass {
     const void *pfn = nullptr;
+    int phase = 0;                 // 0: full passes of every grid; 1: remainder passes
     dim3 grid, block;
     size_t smem = 0;
     stn::BatchArgs args{};
@@ -744,67 +745,73 @@ std::vector<char> batch_key(const stencil_batch_item *items, int n, int dev)
 
 int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cudaStream_t st, BatchEntry *E)
 {
-    struct Item {
-        int idx, L, t;
+    // Every grid runs ceil(iters / t) passes at its own chosen degree t, like stencil_run:
+    // L = iters / t full passes (phase 0), then one remainder pass of degree iters mod t
+    // (phase 1).  Each pass becomes a task of the kernel class that sweeps it.
+    struct Pass1 {
+        int item, pass, phase;
         Pass ps;
-        const stn::KernelEntry *e;
-        int rows;
     };
-    std::vector<Item> it;
+    std::vector<Pass1> passes;
+    std::vector<int> npass(n, 0);
     for (int i = 0; i < n; ++i) {
         const stencil_batch_item &b = items[i];
         stencil_plan *h = b.h;
         stencil_schedule s;
         chosen_schedule(h, b.nx, b.ny, b.nz, b.dtype, &s);
         if (s.kernel != STENCIL_KERNEL_STREAM) return STENCIL_ERR_UNSUPPORTED;
-        // largest compiled degree <= the chosen one that divides iters
-        int t = std::max(1, std::min(s.t, b.iters));
-        while (t > 1 && (b.iters % t != 0 || !registry().find(h->dim, h->r, t, h->dim == 3 ? s.rows_per_thread : 1,
-                                                                b.dtype, h->kind(), s.threads_x, s.threads_y)))
-            --t;
-        s.t = t;
-        Item x;
-        x.idx = i;
-        x.t = t;
-        x.L = b.iters / t;
-        x.rows = h->dim == 3 ? s.rows_per_thread : 1;
-        int rc = plan_pass(h, b.nx, b.ny, b.nz, b.dtype, t, s, dev, x.ps, true);
-        if (rc) return rc;
-        x.e = x.ps.e;
-        x.ps.a.timeout_ms = h->timeout_ms;
-        it.push_back(x);
-    }
-    // scratch grids
-    E->scratch.assign(n, nullptr);
-    for (const Item &x : it)
-        if (x.L > 1) {
-            const stencil_batch_item &b = items[x.idx];
-            const size_t bytes = static_cast<size_t>(b.nx * b.ny * b.nz) * elem_bytes(b.dtype);
-            CK(cudaMalloc(&E->scratch[x.idx], bytes));
+        const int t = std::max(1, std::min(s.t, b.iters));
+        const int full = b.iters / t, rem = b.iters % t;
+        npass[i] = full + (rem ? 1 : 0);
+        for (int p = 0; p < npass[i]; ++p) {
+            Pass1 x;
+            x.item = i;
+            x.pass = p;
+            x.phase = p < full ? 0 : 1;
+            if (p == 0 || p == full) {
+                const int rc = plan_pass(h, b.nx, b.ny, b.nz, b.dtype, p < full ? t : rem, s, dev, x.ps, true);
+                if (rc) return rc;
+                x.ps.a.timeout_ms = h->timeout_ms;
+            } else {
+                x.ps = passes.back().ps;
+            }
+            passes.push_back(x);
         }
-    // group by kernel class, largest grids first inside a class
-    std::vector<const stn::KernelEntry *> kinds;
-    for (const Item &x : it)
-        if (std::find(kinds.begin(), kinds.end(), x.e) == kinds.end()) kinds.push_back(x.e);
-    for (const stn::KernelEntry *kind : kinds) {
-        std::vector<const Item *> mine;
-        for (const Item &x : it)
-            if (x.e == kind) mine.push_back(&x);
-        std::sort(mine.begin(), mine.end(), [](const Item *a, const Item *b) { return a->ps.grid.x > b->ps.grid.x; });
-        int maxL = 0;
-        for (const Item *x : mine) maxL = std::max(maxL, x->L);
-        std::vector<stn::SweepArgs> args;
-        std::vector<CUtensorMap> maps;
-        std::vector<stn::BatchTask> tasks;
-        std::vector<int> last_task(n, -1);
-        int total = 0, fault_task = -1, timeout = 2000;
-        for (int p = 0; p < maxL; ++p)
-            for (const Item *x : mine) {
-                if (p >= x->L) continue;
-                const stencil_batch_item &b = items[x->idx];
-                void *scr = E->scratch[x->idx];
-                const void *src = p == 0 ? b.in : ((x->L - p) % 2 == 0 ? b.out : scr);
-                void *dst = ((x->L - 1 - p) % 2 == 0) ? b.out : scr;
+    }
+    // scratch grids (the second buffer of each grid's ping-pong)
+    E->scratch.assign(n, nullptr);
+    for (int i = 0; i < n; ++i)
+        if (npass[i] > 1) {
+            const stencil_batch_item &b = items[i];
+            const size_t bytes = static_cast<size_t>(b.nx * b.ny * b.nz) * elem_bytes(b.dtype);
+            CK(cudaMalloc(&E->scratch[i], bytes));
+        }
+    // kernel classes per phase; inside a class, tasks pass-major, largest grids first, so every
+    // tile a block waits for was taken earlier by a running block of the same class
+    for (int phase = 0; phase < 2; ++phase) {
+        std::vector<const stn::KernelEntry *> kinds;
+        for (const Pass1 &x : passes)
+            if (x.phase == phase && std::find(kinds.begin(), kinds.end(), x.ps.e) == kinds.end())
+                kinds.push_back(x.ps.e);
+        for (const stn::KernelEntry *kind : kinds) {
+            std::vector<const Pass1 *> mine;
+            for (const Pass1 &x : passes)
+                if (x.phase == phase && x.ps.e == kind) mine.push_back(&x);
+            std::stable_sort(mine.begin(), mine.end(), [](const Pass1 *a, const Pass1 *b) {
+                if (a->pass != b->pass) return a->pass < b->pass;
+                return a->ps.grid.x > b->ps.grid.x;
+            });
+            std::vector<stn::SweepArgs> args;
+            std::vector<CUtensorMap> maps;
+            std::vector<stn::BatchTask> tasks;
+            std::vector<int> last_task(n, -1);
+            int total = 0, fault_task = -1, timeout = 2000;
+            for (const Pass1 *x : mine) {
+                const stencil_batch_item &b = items[x->item];
+                const int L = npass[x->item], p = x->pass;
+                void *scr = E->scratch[x->item];
+                const void *src = p == 0 ? b.in : ((L - p) % 2 == 0 ? b.out : scr);
+                void *dst = ((L - 1 - p) % 2 == 0) ? b.out : scr;
                 stn::SweepArgs a = x->ps.a;
                 a.in = src;
                 a.out = dst;
@@ -812,73 +819,100 @@ int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cuda
                 CUtensorMap m;
                 std::memset(&m, 0, sizeof(m));
                 if (b.h->dim == 3) {
-                    int rc = encode_map(&m, src, b.nx, b.ny, b.nz, b.dtype, 4 * kind->tx + 2 * kind->padin,
-                                        kind->ty * x->rows + 2 * b.h->r);
+                    const int rc = encode_map(&m, src, b.nx, b.ny, b.nz, b.dtype, 4 * kind->tx + 2 * kind->padin,
+                                              kind->ty * kind->vy + 2 * b.h->r);
                     if (rc) return rc;
                 }
                 maps.push_back(m);
                 stn::BatchTask tk;
-                tk.prev = last_task[x->idx];
+                tk.prev = last_task[x->item];   // the grid's previous pass in this class (phase 0)
                 tk.ntiles = static_cast<int>(x->ps.grid.x);
                 tk.first = total;
                 total += tk.ntiles;
                 if (b.h->fault_plane == p && fault_task < 0) fault_task = static_cast<int>(tasks.size());
                 timeout = b.h->timeout_ms;
-                last_task[x->idx] = static_cast<int>(tasks.size());
+                last_task[x->item] = static_cast<int>(tasks.size());
                 tasks.push_back(tk);
             }
-        BatchClass c;
-        c.pfn = kind->pfn;
-        c.block = dim3(kind->tx, kind->ty);
-        c.smem = kind->smem;
-        int rc = prepare_fn(c.pfn, dev.max_smem);
-        if (rc) return rc;
-        int occ = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.pfn, kind->tx * kind->ty, kind->smem));
-        if (occ < 1) return STENCIL_ERR_UNSUPPORTED;
-        c.grid = dim3(static_cast<unsigned>(std::min<int64_t>(total, static_cast<int64_t>(dev.sms) * occ)));
-        const int nt = static_cast<int>(tasks.size());
-        CK(cudaMalloc(&c.dev_args, sizeof(stn::SweepArgs) * nt));
-        CK(cudaMalloc(&c.dev_maps, sizeof(CUtensorMap) * nt));
-        CK(cudaMalloc(&c.dev_tasks, sizeof(stn::BatchTask) * nt));
-        CK(cudaMalloc(&c.dev_done, sizeof(int) * (nt + 1)));
-        CK(cudaMemcpy(c.dev_args, args.data(), sizeof(stn::SweepArgs) * nt, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(c.dev_maps, maps.data(), sizeof(CUtensorMap) * nt, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(c.dev_tasks, tasks.data(), sizeof(stn::BatchTask) * nt, cudaMemcpyHostToDevice));
-        stn::BatchArgs &B = c.args;
-        B.args = static_cast<const stn::SweepArgs *>(c.dev_args);
-        B.maps = static_cast<const CUtensorMap *>(c.dev_maps);
-        B.tasks = static_cast<const stn::BatchTask *>(c.dev_tasks);
-        B.done = static_cast<int *>(c.dev_done);
-        B.head = static_cast<int *>(c.dev_done) + nt;
-        B.status = dev.status;
-        B.ntasks = nt;
-        B.total = total;
-        B.timeout_ms = timeout;
-        B.fault_task = fault_task;
-        E->classes.push_back(c);
+            BatchClass c;
+            c.pfn = kind->pfn;
+            c.phase = phase;
+            c.block = dim3(kind->tx, kind->ty);
+            c.smem = kind->smem;
+            int rc = prepare_fn(c.pfn, dev.max_smem);
+            if (rc) return rc;
+            int occ = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.pfn, kind->tx * kind->ty, kind->smem));
+            if (occ < 1) return STENCIL_ERR_UNSUPPORTED;
+            c.grid = dim3(static_cast<unsigned>(std::min<int64_t>(total, static_cast<int64_t>(dev.sms) * occ)));
+            const int nt = static_cast<int>(tasks.size());
+            CK(cudaMalloc(&c.dev_args, sizeof(stn::SweepArgs) * nt));
+            CK(cudaMalloc(&c.dev_maps, sizeof(CUtensorMap) * nt));
+            CK(cudaMalloc(&c.dev_tasks, sizeof(stn::BatchTask) * nt));
+            CK(cudaMalloc(&c.dev_done, sizeof(int) * (nt + 1)));
+            CK(cudaMemcpy(c.dev_args, args.data(), sizeof(stn::SweepArgs) * nt, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c.dev_maps, maps.data(), sizeof(CUtensorMap) * nt, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c.dev_tasks, tasks.data(), sizeof(stn::BatchTask) * nt, cudaMemcpyHostToDevice));
+            stn::BatchArgs &B = c.args;
+            B.args = static_cast<const stn::SweepArgs *>(c.dev_args);
+            B.maps = static_cast<const CUtensorMap *>(c.dev_maps);
+            B.tasks = static_cast<const stn::BatchTask *>(c.dev_tasks);
+            B.done = static_cast<int *>(c.dev_done);
+            B.head = static_cast<int *>(c.dev_done) + nt;
+            B.status = dev.status;
+            B.ntasks = nt;
+            B.total = total;
+            B.timeout_ms = timeout;
+            B.fault_task = fault_task;
+            E->classes.push_back(c);
+        }
     }
-    // one CUDA graph: per class, reset its counters and run its persistent launch.  It is
-    // captured on a private stream (the caller's may be the legacy stream, which cannot be
-    // captured) and launched on the caller's stream.
+    // One CUDA graph.  Phase 0: every class resets its counters and runs its persistent launch
+    // on a branch of its own, so the classes run side by side (one class's tail overlaps the
+    // others' work; no class waits on another).  Phase 1, after all of phase 0: the remainder
+    // passes, again one branch per class.  Captured on private streams (the caller's may be the
+    // legacy stream, which cannot be captured) and launched on the caller's stream.
     (void)st;
-    cudaStream_t cap = nullptr;
-    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    const int nc = static_cast<int>(E->classes.size());
+    std::vector<cudaStream_t> br(nc + 1, nullptr);
+    std::vector<cudaEvent_t> ev(nc + 2, nullptr);
+    cudaError_t err = cudaSuccess;
+    for (auto &x : br)
+        if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+    for (auto &x : ev)
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
     cudaGraph_t graph = nullptr;
-    cudaError_t err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    cudaStream_t cap = br[nc];
+    if (err == cudaSuccess) err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (err == cudaSuccess) {
-        for (auto &c : E->classes) {
-            if (err == cudaSuccess)
-                err = cudaMemsetAsync(c.dev_done, 0, sizeof(int) * (c.args.ntasks + 1), cap);
-            void *args[] = {&c.args};
-            if (err == cudaSuccess) err = cudaLaunchKernel(c.pfn, c.grid, c.block, args, c.smem, cap);
+        for (int phase = 0; phase < 2; ++phase) {
+            // fork: every class of this phase starts after everything captured so far
+            if (err == cudaSuccess) err = cudaEventRecord(ev[nc], cap);
+            std::vector<int> used;
+            for (int k = 0; k < nc; ++k) {
+                BatchClass &c = E->classes[k];
+                if (c.phase != phase) continue;
+                if (err == cudaSuccess) err = cudaStreamWaitEvent(br[k], ev[nc], 0);
+                if (err == cudaSuccess)
+                    err = cudaMemsetAsync(c.dev_done, 0, sizeof(int) * (c.args.ntasks + 1), br[k]);
+                void *args[] = {&c.args};
+                if (err == cudaSuccess) err = cudaLaunchKernel(c.pfn, c.grid, c.block, args, c.smem, br[k]);
+                if (err == cudaSuccess) err = cudaEventRecord(ev[k], br[k]);
+                used.push_back(k);
+            }
+            // join
+            for (int k : used)
+                if (err == cudaSuccess) err = cudaStreamWaitEvent(cap, ev[k], 0);
         }
         const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
         if (err == cudaSuccess) err = e2;
     }
     if (err == cudaSuccess) err = cudaGraphInstantiate(&E->exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
-    cudaStreamDestroy(cap);
+    for (auto x : ev)
+        if (x) cudaEventDestroy(x);
+    for (auto x : br)
+        if (x) cudaStreamDestroy(x);
     if (err != cudaSuccess) return cuda_fail(err, __LINE__);
     return 0;
 }

@@ -3,8 +3,8 @@
 A mixed batch (2D and 3D, radius 1..4, FP32 and BF16, different step counts)
 must give every grid the oracle's result: FP32 bit for bit; BF16 bit for bit
 against the FP32 oracle run pass by pass with rounding between passes, at the
-temporal degree the batch uses for that grid (the largest compiled degree not
-above the default that divides the step count)."""
+temporal degree the batch uses for that grid (its default degree, passes of t
+steps then a remainder pass, exactly like stencil_run)."""
 import numpy as np
 import pytest
 import torch
@@ -25,11 +25,7 @@ MIX = [  # dim, r, (ny, nx) or (nz, ny, nx), iters, dtype
 
 
 def batch_degree(s, shape, dim, iters, code):
-    nx, ny, nz = (shape[1], shape[0], 1) if dim == 2 else shape[::-1]
-    t = min(s.default_schedule(shape, code).t, iters)
-    while t > 1 and iters % t:
-        t -= 1
-    return t
+    return min(s.default_schedule(shape, code).t, iters)
 
 
 def make_batch(mix, seed=30):
@@ -105,13 +101,43 @@ def test_batch_dependency_wait_times_out_without_hanging():
     """Pass 0 of one grid never reports completion: its next pass's bounded waits expire,
     the status records it and the context keeps working."""
     torch.cuda.set_device(0)
-    mix = [(2, 1, (256, 512), 6, "f32"), (2, 1, (128, 264), 6, "f32")]
+    mix = [(2, 1, (256, 512), 12, "f32"), (2, 1, (128, 264), 12, "f32")]   # three passes of t = 4
     batch = make_batch(mix)
     st.stencil_set_fault_injection(batch[0]["s"].handle, 0, 50)
     assert st.stencil_get_device_status(clear=True) == 0
     st.stencil_run_batched(items_of(batch), torch.cuda.current_stream().cuda_stream)
     assert st.stencil_get_device_status(clear=True) == st.STENCIL_ERR_TIMEOUT
     st.stencil_set_fault_injection(batch[0]["s"].handle, -1, 0)
+    st.stencil_run_batched(items_of(batch), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert st.stencil_get_device_status() == 0
+    check(batch)
+
+
+def test_remainder_passes_and_single_pass_grids():
+    """Step counts that are not multiples of the degree get a remainder pass (its own kernel
+    class, after every full pass); grids with fewer steps than the degree run one pass."""
+    torch.cuda.set_device(0)
+    mix = [(2, 1, (200, 512), 9, "f32"), (2, 2, (120, 256), 7, "bf16"), (2, 4, (90, 264), 5, "f32"),
+           (3, 1, (30, 20, 48), 5, "bf16"), (2, 1, (64, 128), 3, "f32"), (3, 2, (16, 16, 16), 1, "f32")]
+    batch = make_batch(mix, seed=60)
+    st.stencil_run_batched(items_of(batch), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert st.stencil_get_device_status() == 0
+    check(batch)
+
+
+def test_batched_workload_96_grids_matches_oracle():
+    """The batched workload: 96 seeded grids (64 2D sides 512-8192, 32 3D sides 64-384, radius
+    1-4, FP32 and BF16, rows rounded down to 8 cells), 100 steps each, in one call; every
+    grid against the oracle."""
+    torch.cuda.set_device(0)
+    mix = []
+    for it in gen.batch_list():
+        nx = it["nx"] - it["nx"] % 8
+        shape = (it["ny"], nx) if it["dim"] == 2 else (it["nz"], it["ny"], nx)
+        mix.append((it["dim"], it["r"], shape, 100, it["dtype"]))
+    batch = make_batch(mix, seed=100)
     st.stencil_run_batched(items_of(batch), torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     assert st.stencil_get_device_status() == 0
