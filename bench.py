@@ -641,6 +641,64 @@ def measure_batched(stream):
     return res
 
 
+def model_accuracy_main(args):
+    """Analytic model against measurement on the benchmark configurations (the paper's Table III
+    "Model Accuracy" column, measured / estimated, and its model-guided choice of par_time,
+    Section VI.A): per configuration and radius, measured / analytic time at the default
+    schedule, the analytic model's best temporal degree against the measured best, and the
+    regret of the analytic pick.  Every candidate is timed by stencil_tune's exhaustive mode
+    (timing grids: the library's own, values do not change the speed)."""
+    import torch
+    import paper_2002_05983_gb300 as st
+    from paper_2002_05983_gb300 import tune
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    confs = [("2D 16384^2 FP32", 2, 16384, st.STENCIL_F32, RADII), ("3D 512^3 FP32", 3, 512, st.STENCIL_F32, RADII),
+             ("3D 768^3 BF16", 3, 768, st.STENCIL_BF16, (4,)), ("3D 768^3 FP16", 3, 768, st.STENCIL_F16, (4,)),
+             ("2D 32768^2 BF16", 2, 32768, st.STENCIL_BF16, (4,)), ("2D 32768^2 FP16", 2, 32768, st.STENCIL_F16, (4,))]
+    tdt = {st.STENCIL_F32: torch.float32, st.STENCIL_BF16: torch.bfloat16, st.STENCIL_F16: torch.float16}
+    for name, dim, n, dt, radii in confs:
+        shape = (n,) * dim
+        nx, ny, nz = (n, n, 1) if dim == 2 else (n, n, n)
+        x = torch.rand(shape, device="cuda").to(tdt[dt])
+        out = torch.empty_like(x)
+        for r in radii:
+            s = st.Stencil(dim, r, gen.coefficients(dim, r))
+            d = s.default_schedule(shape, dt)
+            iters = 8 * d.t
+            sec = _event_time(lambda: s.run(x, iters, out=out), 2, stream)
+            meas_def = sec * 1e9 / (x.numel() * iters)
+            ana_def = 2.0 ** float(st.stencil_schedule_features(s.handle, nx, ny, nz, dt, d)[11])
+            _, rows = st.stencil_tune(s.handle, nx, ny, nz, dt, st.TUNE_EXHAUSTIVE, store=False, cap=512)
+            meas = np.array([t.ns_per_cell for t in rows])
+            ana = np.array([t.analytic_ns_per_cell for t in rows])
+            per_t = {}
+            for t, mv, av in zip(rows, meas, ana):
+                k = int(t.sched.t)
+                per_t.setdefault(k, [1e30, 1e30])
+                per_t[k] = [min(per_t[k][0], mv), min(per_t[k][1], av)]
+            best_meas_t = min(per_t, key=lambda k: per_t[k][0])
+            best_ana_t = min(per_t, key=lambda k: per_t[k][1])
+            ia, im = int(np.argmin(ana)), int(np.argmin(meas))
+            _row(model_accuracy=True, config=name, dim=dim, r=r, default_t=d.t, default_planes_per_step=d.planes_per_step,
+                 measured_over_analytic_at_default=round(meas_def / ana_def, 3),
+                 gcells_default=round(1.0 / meas_def, 1), gcells_analytic_default=round(1.0 / ana_def, 1),
+                 best_t_analytic=best_ana_t, best_t_measured=best_meas_t,
+                 analytic_pick=dict(t=rows[ia].sched.t, planes_per_step=rows[ia].sched.planes_per_step,
+                                    seg=rows[ia].sched.seg, rows_per_thread=rows[ia].sched.rows_per_thread),
+                 measured_best=dict(t=rows[im].sched.t, planes_per_step=rows[im].sched.planes_per_step,
+                                    seg=rows[im].sched.seg, rows_per_thread=rows[im].sched.rows_per_thread),
+                 regret_analytic_pick=round(tune.regret_of(meas, ia), 4),
+                 regret_default=round(max(meas_def / meas.min() - 1.0, 0.0), 4),
+                 per_t={k: dict(measured_gcells=round(1.0 / v[0], 1), analytic_gcells=round(1.0 / v[1], 1))
+                        for k, v in sorted(per_t.items())})
+            s.close()
+        del x, out
+        torch.cuda.empty_cache()
+    assert st.stencil_get_device_status() == 0
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -656,6 +714,8 @@ def main():
                     help="radii of the sweep2d/sweep3d suites (1..6; the paper's range is 1..4)")
     ap.add_argument("--tune-eval", action="store_true",
                     help="measure all schedules of seeded problems, train the cost model, report regret")
+    ap.add_argument("--model-accuracy", action="store_true",
+                    help="analytic model vs measurement on the benchmark configurations (Table III form)")
     ap.add_argument("--case", default=None,
                     help="single sweep for profiling: dim:r:t:n:iters[:dtype] (grid n^dim, t=0 auto)")
     args = ap.parse_args()
@@ -665,6 +725,8 @@ def main():
         return case_main(args)
     if args.tune_eval:
         return tune_main(args)
+    if args.model_accuracy:
+        return model_accuracy_main(args)
     if args.suite:
         return suite_main(args)
 

@@ -97,7 +97,7 @@ typedef struct {
 } stencil_schedule;
 
 /* Number of features describing one (problem, schedule) pair for the cost model. */
-#define STENCIL_NFEAT 14
+#define STENCIL_NFEAT 18
 
 /* One measured or predicted schedule of a problem (stencil_tune output). */
 typedef struct {
@@ -167,24 +167,31 @@ int stencil_run_host(stencil_handle h, const void *in_host, void *out_host, int6
                      int64_t ny, int64_t nz, int iters, int dtype, void *stream,
                      const stencil_schedule *sched);
 
-/* The schedule stencil_run would use for this problem when given none: the
- * library's rule, overridden by a pick stored in the tuning-cache file (see
- * stencil_tune), overridden by a pick stored on the handle. */
+/* The schedule stencil_run would use for this problem when given none: a pick
+ * stored on the handle (stencil_tune with store != 0), else one stored in the
+ * tuning-cache file (see stencil_tune), else the proposal of the cost model set
+ * with stencil_use_cost_model, else the library's rule (2D: radius 1 at t = 4
+ * with one row per step, radius 2..4 at t = 3, 2, 2 with two rows per step,
+ * radius 5, 6 at t = 2; 3D: t = 2 for radius 1, else t = 1, 2 rows per thread). */
 int stencil_default_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
                              stencil_schedule *out);
 
 /* Schedule tuner (the model-guided parameter choice of Sections V.A and VI.A,
- * re-done for the GPU).  Candidates: every compiled temporal degree, several
- * stream-segment lengths and, in 3D, 2 or 4 rows per thread.
- *  - ANALYTIC: time per cell update = max(HBM bytes / bandwidth, FP32
- *    instructions incl. halo redundancy / (issue rate x an efficiency that
- *    falls with the resident warps per SM)) per pass, divided by the cell
- *    updates of the pass; no device work.
+ * re-done for the GPU).  Candidates: every compiled temporal degree, one or two
+ * rows per step (2D), several stream-segment lengths and, in 3D, 2 or 4 rows
+ * per thread.
+ *  - ANALYTIC: time per cell update = max(HBM bytes / bandwidth, issue time)
+ *    per pass, divided by the cell updates of the pass; the issue time counts
+ *    per step and level every thread's FP32 chains (halo cells included) and
+ *    its bookkeeping instructions, at a share of the SM issue rate that falls
+ *    with the resident warps per SM; no device work.
  *  - EXHAUSTIVE: allocates an input and output grid of the problem's size
  *    (cudaMalloc), runs each candidate for >= 16 steps after a warm-up, takes
  *    the best of two CUDA-event timings, frees the grids; synchronous.
- *  - MODEL: needs `model` (stencil_model_train); no device work besides the
- *    model's forward pass.
+ *  - MODEL: needs `model` (stencil_model_train), trained to predict
+ *    log(measured / analytic time) from the features; the prediction of a
+ *    candidate is its analytic time times exp(model output).  No device work
+ *    besides the model's forward pass.
  * `chosen` receives the pick; `rows` (capacity `cap`, may be NULL) receives one
  * stencil_timing per candidate and *nrows their number.  With `store` != 0 the
  * pick is kept in the handle and used by later stencil_run calls on the same
@@ -200,11 +207,13 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
 
 /* Features of (problem, schedule) for the cost model: dim, radius, log2 nx,
  * log2 ny, log2 nz, bytes per element, t, resident warps per SM, tile height
- * (rows, 1 in 2D), log2 of the unrolled loop body's FMA count
- * ((2r+1) * t * 4 * rows * (2*dim*r+1)), log2 segment length, log2 analytic
- * ns per cell update, block order (1: 2D strips laid end to end, 0: slabs),
- * log2 of the launch's blocks per resident block slot (waves).  `sched` may
- * be partial (0 = library choice). */
+ * (rows, 1 in 2D), log2 of the unrolled loop body's FMA count (queue period x
+ * t x 4 x rows x (2*dim*r+1)), log2 segment length, log2 analytic ns per cell
+ * update, block order (1: 2D strips laid end to end, 0: slabs), log2 of the
+ * launch's blocks per resident block slot (waves), rows per step, log2 halo
+ * redundancy (thread region over compute tile), registers per thread / 64,
+ * log2 dynamic shared memory in KiB.  `sched` may be partial (0 = library
+ * choice). */
 int stencil_schedule_features(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
                               const stencil_schedule *sched, float *features);
 
@@ -231,6 +240,15 @@ int stencil_model_params(stencil_model_handle m, float *host, int count, int set
  * respect to the flat parameters, for testing the backward kernels. */
 int stencil_model_grad(stencil_model_handle m, const float *X, const float *y, int n, float *loss,
                        float *grad);
+
+/* Make `m` (trained as stencil_tune's MODEL mode expects) the process-wide cost
+ * model that proposes schedules: stencil_run, stencil_run_batched and
+ * stencil_default_schedule then use, for a problem with no pick stored on the
+ * handle or in the tuning-cache file, the candidate with the lowest predicted
+ * time (computed once per handle and problem; one small forward pass of the
+ * model on the current device).  NULL restores the library's built-in rule.
+ * The model must stay alive while it is in use.  Never fails (STENCIL_OK). */
+int stencil_use_cost_model(stencil_model_handle m);
 
 /* Largest temporal degree compiled in for (dim, radius, dtype) and, in 3D,
  * rows_per_thread; 0 if none.  */

@@ -34,10 +34,10 @@ EXPORTS = ("stencil_create", "stencil_create_shared", "stencil_destroy", "stenci
            "stencil_set_fault_injection", "stencil_set_checked", "stencil_run_noalloc", "stencil_run_batched", "stencil_tune",
            "stencil_schedule_features", "stencil_model_create", "stencil_model_destroy",
            "stencil_model_train", "stencil_model_predict", "stencil_model_normalization",
-           "stencil_model_params", "stencil_model_grad", "stencil_measure_peaks", "stencil_last_cuda_error",
+           "stencil_model_params", "stencil_model_grad", "stencil_use_cost_model", "stencil_measure_peaks", "stencil_last_cuda_error",
            "stencil_strerror")
 
-NFEAT = 14
+NFEAT = 18
 TUNE_ANALYTIC, TUNE_EXHAUSTIVE, TUNE_MODEL = 0, 1, 2
 
 
@@ -115,6 +115,7 @@ def _lib():
                 lib.stencil_model_params.argtypes = [vp, fp, i32, i32]
                 lib.stencil_model_grad.argtypes = [vp, fp, fp, i32, fp, fp]
                 lib.stencil_measure_peaks.argtypes = [vp, ctypes.POINTER(Peaks)]
+                lib.stencil_use_cost_model.argtypes = [vp]
                 lib.stencil_last_cuda_error.argtypes = []
                 lib.stencil_strerror.argtypes = [i32]
                 lib.stencil_strerror.restype = ctypes.c_char_p
@@ -298,6 +299,11 @@ def stencil_model_grad(m, X, y):
     loss = np.zeros(1, np.float32)
     _check(_lib().stencil_model_grad(m, _fptr(X), _fptr(y), len(y), _fptr(loss), _fptr(g)), "stencil_model_grad")
     return float(loss[0]), g
+
+
+def stencil_use_cost_model(m) -> int:
+    """Let model `m` (None: the built-in rule) propose the default schedules."""
+    return _check(_lib().stencil_use_cost_model(m), "stencil_use_cost_model")
 
 
 def stencil_measure_peaks(stream=None) -> Peaks:

@@ -11,6 +11,7 @@ struct KernelEntry {
     int sh;                     // bit 0: one coefficient per distance; bit 1: bounds-checked build
     int tx, ty;                 // block shape
     int p;                      // planes every level advances per step (2D rows: 1 or 2; 3D: 1)
+    int qp, u, rot;             // register-queue period (planes), steps per unrolled chunk, rotating queue
     int cx, cy, htx, hty;       // compute tile and thread-region halo
     int pf;                     // planes loaded ahead of use
     int padin;                  // input-plane x padding per side (cells): TMA box width 4*tx + 2*padin
@@ -70,7 +71,9 @@ int list_2d_f16_p2(const KernelEntry **e);
 #define STN_EX(D, R, T, VY, S, DT, TX, TY, SH) STN_EXC(D, R, T, VY, S, DT, TX, TY, SH, false, 1)
 // kind = SH + 2 * CHK: coefficient form and bounds-checked build; P planes per step
 #define STN_EXC(D, R, T, VY, S, DT, TX, TY, SH, CHK, P)                                            \
-    {D, R, T, VY, DT, (SH ? 1 : 0) + (CHK ? 2 : 0), TX, TY, P, STN_G(D, R, T, VY, S, TX, TY, P)::CX,  \
+    {D, R, T, VY, DT, (SH ? 1 : 0) + (CHK ? 2 : 0), TX, TY, P, STN_G(D, R, T, VY, S, TX, TY, P)::QP,  \
+     STN_G(D, R, T, VY, S, TX, TY, P)::U, STN_G(D, R, T, VY, S, TX, TY, P)::ROT ? 1 : 0,              \
+     STN_G(D, R, T, VY, S, TX, TY, P)::CX,                                                          \
      STN_G(D, R, T, VY, S, TX, TY, P)::CY,                                                          \
      STN_G(D, R, T, VY, S, TX, TY, P)::HTX, STN_G(D, R, T, VY, S, TX, TY, P)::HTY,                  \
      STN_G(D, R, T, VY, S, TX, TY, P)::PF, STN_G(D, R, T, VY, S, TX, TY, P)::PADIN,                 \

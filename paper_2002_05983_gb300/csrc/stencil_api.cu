@@ -42,6 +42,13 @@ struct stencil_plan {
         stencil_schedule s;
     };
     std::vector<Tuned> tuned;   // schedules stored by stencil_tune
+    struct ModelPick {
+        int64_t nx, ny, nz;
+        int dtype;
+        unsigned gen;           // cost-model generation the pick was made with
+        stencil_schedule s;
+    };
+    mutable std::vector<ModelPick> model_picks;   // default picks proposed by the active cost model
 };
 
 namespace {
@@ -123,15 +130,23 @@ const Registry &registry()
 std::mutex g_attr_mu;
 std::vector<const void *> g_attr_done;
 
-int prepare_fn(const void *fn, int max_smem)
+std::vector<int> g_attr_regs;   // registers per thread of each prepared function
+
+int prepare_fn(const void *fn, int max_smem, int *regs = nullptr)
 {
     std::lock_guard<std::mutex> lk(g_attr_mu);
-    if (std::find(g_attr_done.begin(), g_attr_done.end(), fn) != g_attr_done.end()) return 0;
+    const auto it = std::find(g_attr_done.begin(), g_attr_done.end(), fn);
+    if (it != g_attr_done.end()) {
+        if (regs) *regs = g_attr_regs[static_cast<size_t>(it - g_attr_done.begin())];
+        return 0;
+    }
     cudaFuncAttributes fa;
     CK(cudaFuncGetAttributes(&fa, fn));   // static shared memory counts against the same limit
     CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             max_smem - static_cast<int>(fa.sharedSizeBytes)));
     g_attr_done.push_back(fn);
+    g_attr_regs.push_back(fa.numRegs);
+    if (regs) *regs = fa.numRegs;
     return 0;
 }
 
@@ -185,6 +200,7 @@ struct Pass {
     const stn::KernelEntry *e = nullptr;   // the kernel's registry entry
     int t = 0;
     int occ = 0;   // resident blocks per SM
+    int regs = 0;  // registers per thread of the kernel
     int padin = 0; // input-plane x padding per side: 3D tensor-map box width 4*block.x + 2*padin
     dim3 grid, block;
     size_t smem = 0;
@@ -323,14 +339,44 @@ void fc_store(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
     g_fc.push_back({gpu, h->dim, h->r, h->kind(), dtype, nx, ny, nz, s});
 }
 
-// The schedule stencil_run uses when the caller gives none: the default rule, overridden
-// by a pick stored in the tuning-cache file, overridden by one stored on the handle.
+// The cost model that proposes default schedules (stencil_use_cost_model), and a generation
+// count that retires the picks made with an earlier model.
+std::mutex g_model_mu;
+stencil_model_handle g_model = nullptr;
+unsigned g_model_gen = 0;
+
+// The schedule stencil_run uses when the caller gives none: a pick stored on the handle,
+// else one in the tuning-cache file, else the active cost model's proposal, else the
+// library's rule.
 void chosen_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, stencil_schedule *s)
 {
     default_schedule(h, nx, ny, nz, dtype, s);
-    fc_lookup(h, nx, ny, nz, dtype, s);
+    bool picked = fc_lookup(h, nx, ny, nz, dtype, s);
     for (const auto &tu : h->tuned)
-        if (tu.nx == nx && tu.ny == ny && tu.nz == nz && tu.dtype == dtype) *s = tu.s;
+        if (tu.nx == nx && tu.ny == ny && tu.nz == nz && tu.dtype == dtype) {
+            *s = tu.s;
+            picked = true;
+        }
+    if (picked) return;
+    stencil_model_handle m = nullptr;
+    unsigned gen = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_model_mu);
+        m = g_model;
+        gen = g_model_gen;
+    }
+    if (!m || s->kernel != STENCIL_KERNEL_STREAM) return;
+    for (const auto &mp : h->model_picks)
+        if (mp.gen == gen && mp.nx == nx && mp.ny == ny && mp.nz == nz && mp.dtype == dtype) {
+            *s = mp.s;
+            return;
+        }
+    stencil_schedule pick;
+    if (stencil_tune(const_cast<stencil_plan *>(h), nx, ny, nz, dtype, STENCIL_TUNE_MODEL, m, 0, &pick, nullptr, 0,
+                     nullptr) != STENCIL_OK)
+        return;   // keep the library's rule
+    *s = pick;
+    h->model_picks.push_back({nx, ny, nz, dtype, gen, pick});
 }
 
 // Fill one pass of temporal degree t.  Pointers are set by the caller.
@@ -348,7 +394,8 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
     if (!e) return STENCIL_ERR_UNSUPPORTED;
     if (s.prefetch && s.prefetch != e->pf) return STENCIL_ERR_UNSUPPORTED;
     if (e->smem > static_cast<size_t>(dev.max_smem)) return STENCIL_ERR_UNSUPPORTED;
-    int rc = prepare_fn(e->fn, dev.max_smem);
+    int regs = 0;
+    int rc = prepare_fn(e->fn, dev.max_smem, &regs);
     if (rc) return rc;
     int occ = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e->fn, e->tx * e->ty, e->smem));
@@ -395,6 +442,7 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
     ps.e = e;
     ps.t = t;
     ps.occ = occ;
+    ps.regs = regs;
     ps.grid = dim3(static_cast<unsigned>(nblk));
     ps.block = dim3(e->tx, e->ty);
     ps.smem = e->smem;
@@ -588,11 +636,18 @@ int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny,
 
 // ------------------------------------------------------------------------
 // Schedule tuner: candidates, analytic model, features.
-constexpr double kFp32InstrRate = 152.0 * 128.0 * 2.07e9;   // FP32 lane instructions / s (nominal)
-constexpr double kFpEfficiency = 0.42;   // FMA issue share the sweep kernels reach with >= 16 warps/SM
-constexpr double kFullWarps = 16.0;      // resident warps per SM below which latency is exposed
-constexpr double kHbmBytesPerS = 6792.1e9 * 0.92;           // measured copy bandwidth, achievable share
-
+// Issue-slot model of the streaming kernel, calibrated with the profiled kernels' ncu opcode
+// counts and their measured rates: per step and time level a thread issues its 4*VY*P cells'
+// FP32 chains (one FMUL and 2*D*r FFMA per cell) plus bookkeeping (neighbour loads, ring stores,
+// ring addressing, the copy wait and the barrier: 2D about 2.6 + 4.5 r + 13.9 P instructions,
+// 10 P more for level 1's widening loads from a 16-bit ring; 3D the y/x neighbour loads of every
+// row and, for shifting queues, the register moves); warps issue at kIssueEff of the SM's rate
+// once 16 warps per SM hide the latencies.
+constexpr double kLaneIssuePerSmPerClk = 128.0;   // 4 schedulers x 32 lanes
+constexpr double kSmClockHz = 2.07e9;             // maximum SM clock (held under load, clock samples)
+constexpr double kIssueEff = 0.64;                // issue share reached with >= 16 resident warps per SM
+constexpr double kFullWarps = 16.0;               // resident warps per SM below which latency is exposed
+constexpr double kHbmBytesPerS = 6787.6e9 * 0.92; // measured copy bandwidth, achievable share
 // Resolve every field of a schedule for a problem (the pass of degree t).
 int resolve(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, stencil_schedule s,
             const DevInfo &dev, stencil_schedule &out, Pass &ps)
@@ -610,9 +665,11 @@ int resolve(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype
     return 0;
 }
 
-// Analytic time per cell update (ns) of a resolved schedule.
+// Analytic time per cell update (ns) of a resolved schedule: the larger of the HBM time
+// (2 s bytes per cell per pass) and the issue time of the blocks, which run in waves of
+// SMs x occupancy.
 double analytic_ns(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, const stencil_schedule &s,
-                   int occ)
+                   int occ, int sms)
 {
     const int D = h->dim, R = h->r, t = s.t;
     const stn::KernelEntry *e = registry().find(D, R, t, D == 3 ? s.rows_per_thread : 1, dtype, h->kind(), s.threads_x,
@@ -620,26 +677,33 @@ double analytic_ns(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, in
     if (!e) return 1e9;
     const double es = elem_bytes(dtype);
     const double N = static_cast<double>(nx) * ny * nz;
-    const double bx = 4.0 * e->tx, by = D == 3 ? static_cast<double>(e->ty) * e->vy : 1.0;
     const double tiles = std::ceil(nx / static_cast<double>(e->cx)) * (D == 3 ? std::ceil(ny / static_cast<double>(e->cy)) : 1.0);
     const double ns_axis = D == 3 ? static_cast<double>(nz) : static_cast<double>(ny);
     const double nblk = std::ceil(tiles * ns_axis / s.seg);
-    // cell-level updates of one block: its thread region for every level over
-    // its planes plus the r*t stream halo; blocks run in waves of sms*occ
-    const double per_block = bx * by * t * (s.seg + static_cast<double>(t) * R) * (2.0 * D * R + 1.0);
-    const double slots = 152.0 * std::max(occ, 1);
+    const int P = e->p, VY = e->vy, NV = (R + 3) / 4;
+    const double cells = 4.0 * VY * P;                               // per thread, level and step
+    const double fp = cells * (2.0 * D * R + 1.0);   // both coefficient forms: 2*D*r + 1 FP32 instructions
+    const double book = (D == 2 ? 2.6 + 4.5 * R + 13.9 * P
+                                : 20.0 + 2.0 * (2.0 * R + 2.0 * NV) * VY + (e->rot ? 0.0 : 6.0 * VY * e->qp / e->u)) +
+                        (es == 2 ? 10.0 * P / t : 0.0);   // level 1 of t widens its 16-bit neighbour loads
+    // stream planes of a block: its segment, the r*t halo planes and the pipeline fill
+    const double lagT = std::max(R, P) + (t - 1) * (P + std::max(R, P));
+    const double steps = (std::min<double>(s.seg, ns_axis) + 2.0 * t * R + lagT) / P;
+    const double instr = static_cast<double>(e->tx) * e->ty * steps * t * (fp + book);
+    const double slots = static_cast<double>(sms) * std::max(occ, 1);
     const double waves = std::ceil(nblk / slots);
     const double warps = static_cast<double>(occ) * e->tx * e->ty / 32.0;
-    const double eff = kFpEfficiency * std::min(1.0, warps / kFullWarps);
-    const double t_fp = waves * per_block * std::max(occ, 1) / (kFp32InstrRate / 152.0 * std::max(eff, 0.02));
+    const double eff = kIssueEff * std::min(1.0, warps / kFullWarps);
+    const double t_issue = waves * instr * std::max(occ, 1) / (kLaneIssuePerSmPerClk * kSmClockHz * std::max(eff, 0.02));
     const double t_mem = N * 2.0 * es / kHbmBytesPerS;
-    return std::max(t_fp, t_mem) / (N * t) * 1e9;
+    return std::max(t_issue, t_mem) / (N * t) * 1e9;
 }
 
 void features_of(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dtype, const stencil_schedule &s,
-                 const Pass &ps, double analytic, float *f)
+                 const Pass &ps, double analytic, int sms, float *f)
 {
     const int occ = ps.occ;
+    const stn::KernelEntry *e = ps.e;
     f[0] = static_cast<float>(h->dim);
     f[1] = static_cast<float>(h->r);
     f[2] = static_cast<float>(std::log2(static_cast<double>(nx)));
@@ -651,12 +715,18 @@ void features_of(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int 
     f[7] = static_cast<float>(occ * s.threads_x * s.threads_y / 32);   // resident warps per SM
     f[8] = static_cast<float>(h->dim == 3 ? s.threads_y * vy : 1);
     // size of the unrolled loop body: queue period x levels x cells x FMA per cell
-    f[9] = static_cast<float>(std::log2(static_cast<double>(2 * h->r + 1) * s.t * 4 * vy * (2 * h->dim * h->r + 1)));
+    f[9] = static_cast<float>(std::log2(static_cast<double>(e->qp) * s.t * 4 * vy * (2 * h->dim * h->r + 1)));
     f[10] = static_cast<float>(std::log2(static_cast<double>(s.seg)));
     f[11] = static_cast<float>(std::log2(analytic));
     // work partition: block order (strips end to end or slabs) and waves of resident blocks
     f[12] = static_cast<float>(ps.a.flat);
-    f[13] = static_cast<float>(std::log2(static_cast<double>(ps.grid.x) / (152.0 * std::max(occ, 1))));
+    f[13] = static_cast<float>(std::log2(static_cast<double>(ps.grid.x) / (static_cast<double>(sms) * std::max(occ, 1))));
+    // rows per step, halo redundancy (thread region over compute tile), registers, shared memory
+    f[14] = static_cast<float>(e->p);
+    const double reg = 4.0 * e->tx * (h->dim == 3 ? e->ty * e->vy : 1);
+    f[15] = static_cast<float>(std::log2(reg / (static_cast<double>(e->cx) * e->cy)));
+    f[16] = static_cast<float>(ps.regs) / 64.0f;
+    f[17] = static_cast<float>(std::log2(static_cast<double>(e->smem) / 1024.0));
 }
 
 // Candidate schedules (unresolved) of a problem.
@@ -1258,7 +1328,7 @@ int stencil_schedule_features(stencil_handle h, int64_t nx, int64_t ny, int64_t 
     Pass ps;
     rc = resolve(h, nx, ny, nz, dtype, s, *dev, r, ps);
     if (rc) return rc;
-    features_of(h, nx, ny, nz, dtype, r, ps, analytic_ns(h, nx, ny, nz, dtype, r, ps.occ), features);
+    features_of(h, nx, ny, nz, dtype, r, ps, analytic_ns(h, nx, ny, nz, dtype, r, ps.occ, dev->sms), dev->sms, features);
     return STENCIL_OK;
 }
 
@@ -1290,8 +1360,8 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
         if (dup) continue;
         stencil_timing tm{};
         tm.sched = r;
-        tm.analytic_ns_per_cell = static_cast<float>(analytic_ns(h, nx, ny, nz, dtype, r, ps.occ));
-        features_of(h, nx, ny, nz, dtype, r, ps, tm.analytic_ns_per_cell, tm.features);
+        tm.analytic_ns_per_cell = static_cast<float>(analytic_ns(h, nx, ny, nz, dtype, r, ps.occ, dev->sms));
+        features_of(h, nx, ny, nz, dtype, r, ps, tm.analytic_ns_per_cell, dev->sms, tm.features);
         tm.ns_per_cell = -1.f;
         tm.model_ns_per_cell = -1.f;
         tim.push_back(tm);
@@ -1303,7 +1373,8 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
         for (int i = 0; i < nc; ++i) std::memcpy(&X[static_cast<size_t>(i) * STENCIL_NFEAT], tim[i].features, sizeof(tim[i].features));
         rc = stencil_model_predict(model, X.data(), y.data(), nc);
         if (rc) return rc;
-        for (int i = 0; i < nc; ++i) tim[i].model_ns_per_cell = std::exp(y[i]);
+        // the model predicts the log of measured over analytic time
+        for (int i = 0; i < nc; ++i) tim[i].model_ns_per_cell = tim[i].analytic_ns_per_cell * std::exp(y[i]);
     }
     if (mode == STENCIL_TUNE_EXHAUSTIVE) {
         const size_t bytes = static_cast<size_t>(nx * ny * nz) * elem_bytes(dtype);
@@ -1362,6 +1433,14 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
     if (rows)
         for (int i = 0; i < nc && i < cap; ++i) rows[i] = tim[i];
     if (nrows) *nrows = nc;
+    return STENCIL_OK;
+}
+
+int stencil_use_cost_model(stencil_model_handle m)
+{
+    std::lock_guard<std::mutex> lk(g_model_mu);
+    g_model = m;
+    ++g_model_gen;
     return STENCIL_OK;
 }
 

@@ -2,11 +2,13 @@
 
 The paper picks FPGA parameters with a performance model and places and
 routes the top few (Sections V.A and VI.A).  Here the choice of temporal
-degree, stream-segment length and (3D) rows per thread is made by
-``stencil_tune``: exhaustively on the GPU, from the analytic
-bandwidth/compute model, or from a learned cost model (a 2x64 ReLU MLP whose
-forward/backward/Adam kernels are in csrc/mlp.cu).  This module only loops
-over problems and marshals arrays; all timing and training runs in the library.
+degree, rows per step (2D), stream-segment length and (3D) rows per thread is
+made by ``stencil_tune``: exhaustively on the GPU, from the analytic
+bandwidth/issue model, or from a learned cost model (a 2x64 ReLU MLP whose
+forward/backward/Adam kernels are in csrc/mlp.cu) that predicts the log of
+measured over analytic time, i.e. learns the analytic model's error.  This
+module only loops over problems and marshals arrays; all timing and training
+runs in the library.
 """
 from __future__ import annotations
 
@@ -55,15 +57,28 @@ def measure(problems):
 
 
 def database(measured):
-    """Feature matrix X, target y = log(ns per cell update), problem index per row."""
+    """Feature matrix X, target y = log(measured / analytic ns per cell update) (the
+    analytic model's error, which stencil_tune's MODEL mode multiplies back in), problem
+    index per row."""
     X, y, g = [], [], []
     for i, (_, rows) in enumerate(measured):
         for t in rows:
-            if t.ns_per_cell > 0:
+            if t.ns_per_cell > 0 and t.analytic_ns_per_cell > 0:
                 X.append(list(t.features))
-                y.append(math.log(t.ns_per_cell))
+                y.append(math.log(t.ns_per_cell / t.analytic_ns_per_cell))
                 g.append(i)
     return np.asarray(X, np.float32), np.asarray(y, np.float32), np.asarray(g)
+
+
+def same_schedule(a, b) -> bool:
+    return (a.t == b.t and a.seg == b.seg and a.rows_per_thread == b.rows_per_thread
+            and a.planes_per_step == b.planes_per_step)
+
+
+def regret_of(times, pick: int) -> float:
+    """T(pick) / T(best) - 1 over a problem's measured candidate times."""
+    times = np.asarray(times, np.float64)
+    return float(times[pick] / times.min() - 1.0)
 
 
 def train(X, y, epochs=3000, lr=3e-3, seed=0, hidden=64):
@@ -84,9 +99,8 @@ def regret(model, measured):
         for name, mode in (("model", TUNE_MODEL), ("analytic", TUNE_ANALYTIC)):
             ch, _ = stencil_tune(s.handle, p["nx"], p["ny"], p["nz"], p["dtype"], mode,
                                  model=model if mode == TUNE_MODEL else None, store=False)
-            k = [i for i, t in enumerate(rows) if t.sched.t == ch.t and t.sched.seg == ch.seg
-                 and t.sched.rows_per_thread == ch.rows_per_thread]
-            picks[name] = times[k[0]] / best - 1.0 if k else float("nan")
+            k = [i for i, t in enumerate(rows) if same_schedule(t.sched, ch)]
+            picks[name] = regret_of(times, k[0]) if k else float("nan")
         s.close()
         res.append(dict(problem=p, best_ns=best, **{f"regret_{k}": v for k, v in picks.items()}))
     return res

@@ -104,8 +104,7 @@ def test_tune_modes_pick_valid_schedules(dim, r, shape, dt):
     times = [t.ns_per_cell for t in rows]
     assert min(times) > 0
     k = int(np.argmin(times))
-    assert (chosen.t, chosen.seg, chosen.rows_per_thread) == (rows[k].sched.t, rows[k].sched.seg,
-                                                              rows[k].sched.rows_per_thread)
+    assert tune.same_schedule(chosen, rows[k].sched)
     feats = np.array([list(t.features) for t in rows], np.float32)
     assert np.all(np.isfinite(feats))
     # analytic mode stores its pick; stencil_run then uses it and stays bit-exact
@@ -115,15 +114,51 @@ def test_tune_modes_pick_valid_schedules(dim, r, shape, dt):
         f = gen.workload_grid(dim, nx, ny, nz)
         got = s.run(torch.from_numpy(f).cuda(), 2 * a.t + 1).cpu().numpy()
         assert np.array_equal(got, oracle.sweep_f32(f, dim, r, c, 2 * a.t + 1))
-    # model mode with a model trained on these rows
+    # model mode with a model trained on these rows: it predicts log(measured / analytic)
     X = feats
-    yv = np.log([t.ns_per_cell for t in rows]).astype(np.float32)
+    yv = np.log([t.ns_per_cell / t.analytic_ns_per_cell for t in rows]).astype(np.float32)
     m = st.stencil_model_create(st.NFEAT, 64, 0)
     st.stencil_model_train(m, X, yv, epochs=800, lr=3e-3)
     mc, mrows = st.stencil_tune(s.handle, nx, ny, nz, dt, st.TUNE_MODEL, model=m, store=False)
     assert all(t.model_ns_per_cell > 0 for t in mrows)
+    pred = np.array([t.model_ns_per_cell for t in mrows])
+    assert tune.same_schedule(mc, mrows[int(np.argmin(pred))].sched)
+    np.testing.assert_allclose(pred, [t.analytic_ns_per_cell for t in mrows] *
+                               np.exp(st.stencil_model_predict(m, X)), rtol=1e-5)
     st.stencil_model_destroy(m)
     s.close()
+
+
+def test_active_cost_model_proposes_default_schedules():
+    """With stencil_use_cost_model set, a problem without a stored pick runs the model's pick
+    (stays bit-exact); a stored pick still wins; None restores the library's rule."""
+    dim, r, nx, ny = 2, 3, 1024, 520
+    c = gen.coefficients(dim, r)
+    s = st.Stencil(dim, r, c)
+    rule = s.default_schedule((ny, nx))
+    _, rows = st.stencil_tune(s.handle, nx, ny, 1, st.STENCIL_F32, st.TUNE_ANALYTIC, store=False)
+    X = np.array([list(t.features) for t in rows], np.float32)
+    # a model that prefers one temporal degree: predicted error grows away from t = 1
+    yv = np.array([0.5 * (t.sched.t - 1) for t in rows], np.float32)
+    m = st.stencil_model_create(st.NFEAT, 64, 1)
+    st.stencil_model_train(m, X, yv, epochs=1500, lr=3e-3)
+    want, _ = st.stencil_tune(s.handle, nx, ny, 1, st.STENCIL_F32, st.TUNE_MODEL, model=m, store=False)
+    try:
+        st.stencil_use_cost_model(m)
+        fresh = st.Stencil(dim, r, c)
+        got = fresh.default_schedule((ny, nx))
+        assert tune.same_schedule(got, want)
+        f = gen.workload_grid(dim, nx, ny)
+        out = fresh.run(torch.from_numpy(f).cuda(), 5).cpu().numpy()
+        assert np.array_equal(out, oracle.sweep_f32(f, dim, r, c, 5))
+        stored, _ = st.stencil_tune(fresh.handle, nx, ny, 1, st.STENCIL_F32, st.TUNE_ANALYTIC, store=True)
+        assert tune.same_schedule(fresh.default_schedule((ny, nx)), stored)
+    finally:
+        st.stencil_use_cost_model(None)
+    other = st.Stencil(dim, r, c)
+    d = other.default_schedule((ny, nx))
+    assert (d.t, d.planes_per_step, d.seg) == (rule.t, rule.planes_per_step, rule.seg)
+    st.stencil_model_destroy(m)
 
 
 def test_tuning_problem_set_is_streamable():
