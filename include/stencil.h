@@ -92,8 +92,9 @@ typedef struct {
     int seg;             /* stream-axis rows/planes per block, >= 1 */
     int prefetch;        /* 0, or the compiled number of planes loaded ahead */
     int planes_per_step; /* 2D: rows every time level advances per step of the block's loop,
-                            1 or 2 (two rows share one barrier and one copy wait); 3D: 1.
-                            A degree compiled with one row per step only runs with one. */
+                            1, 2 (t = 1..5) or 4 (t = 1): the rows of a step share one
+                            barrier, one copy wait and the loop's bookkeeping; 3D: 1.  A
+                            degree compiled with one row per step only runs with one. */
 } stencil_schedule;
 
 /* Number of features describing one (problem, schedule) pair for the cost model. */
@@ -171,8 +172,9 @@ int stencil_run_host(stencil_handle h, const void *in_host, void *out_host, int6
  * stored on the handle (stencil_tune with store != 0), else one stored in the
  * tuning-cache file (see stencil_tune), else the proposal of the cost model set
  * with stencil_use_cost_model, else the library's rule (2D: radius 1 at t = 4
- * with one row per step, radius 2..4 at t = 3, 2, 2 with two rows per step,
- * radius 5, 6 at t = 2; 3D: t = 2 for radius 1, else t = 1, 2 rows per thread). */
+ * with one row per step, radius 2..4 at t = 3, 2, 2 with two rows per step --
+ * 16-bit storage radius 3 at t = 3 --, radius 5, 6 at t = 2; 3D: t = 2 for
+ * radius 1, else t = 1, 2 rows per thread). */
 int stencil_default_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
                              stencil_schedule *out);
 

@@ -62,6 +62,7 @@ int list_checked(const KernelEntry **e);
 int list_2d_f32_p2(const KernelEntry **e);
 int list_2d_bf16_p2(const KernelEntry **e);
 int list_2d_f16_p2(const KernelEntry **e);
+int list_2d_p4(const KernelEntry **e);
 
 }  // namespace stn
 

@@ -93,7 +93,7 @@ struct Registry {
                            stn::list_3d_bf16_r5, stn::list_3d_bf16_r6, stn::list_2d_f16_r5,
                            stn::list_2d_f16_r6,  stn::list_3d_f16_r5,  stn::list_3d_f16_r6,
                            stn::list_2d_f32sh,   stn::list_3d_f32sh,   stn::list_checked,  stn::list_2d_f32_p2,
-                           stn::list_2d_bf16_p2, stn::list_2d_f16_p2};
+                           stn::list_2d_bf16_p2, stn::list_2d_f16_p2,  stn::list_2d_p4};
         for (L f : lists) {
             const stn::KernelEntry *e = nullptr;
             const int n = f(&e);
@@ -223,10 +223,11 @@ void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz,
     const bool have = reg.max_t(h->dim, h->r, dtype, h->dim == 3 ? 2 : 1, h->kind()) > 0;
     d.kernel = (have && stream_applicable(dtype, nx)) ? STENCIL_KERNEL_STREAM : STENCIL_KERNEL_NAIVE;
     if (h->dim == 2) {
-        // measured on 16384^2 FP32: radius 1 peaks at t = 4 with one row per step; radii
-        // 2-4 gain 12-19 % from two rows per step (t = 3, 2, 2)
+        // measured on 16384^2: radius 1 peaks at t = 4 with one row per step; radii 2-4 gain
+        // 12-19 % from two rows per step (FP32 t = 3, 2, 2; 16-bit storage radius 3 at t = 3)
         static const int t2[stn::kMaxR + 1] = {0, 4, 3, 2, 2, 2, 2};
-        d.t = std::max(1, std::min(t2[h->r], reg.max_t(2, h->r, dtype, 1, h->kind())));
+        static const int t2h[stn::kMaxR + 1] = {0, 4, 3, 3, 2, 2, 2};
+        d.t = std::max(1, std::min(dtype == STENCIL_F32 ? t2[h->r] : t2h[h->r], reg.max_t(2, h->r, dtype, 1, h->kind())));
         d.threads_x = 128;
         d.threads_y = 1;
         d.rows_per_thread = 1;
@@ -577,7 +578,7 @@ int run_impl(stencil_plan *h, const void *in, void *out, int64_t nx, int64_t ny,
         if (user->seg) s.seg = user->seg;
         if (user->prefetch) s.prefetch = user->prefetch;
         if (user->planes_per_step) s.planes_per_step = user->planes_per_step;
-        if (s.t < 0 || s.seg < 0 || s.prefetch < 0 || s.planes_per_step < 0 || s.planes_per_step > 2)
+        if (s.t < 0 || s.seg < 0 || s.prefetch < 0 || s.planes_per_step < 0 || s.planes_per_step > 4)
             return STENCIL_ERR_INVALID_ARG;
         if (h->dim == 3 && user->t && !user->rows_per_thread)
             s.rows_per_thread = 2;

@@ -24,7 +24,7 @@ __host__ __device__ constexpr int rup(int a, int b) { return cdiv(a, b) * b; }
 // ES: bytes per stored element (4 fp32, 2 bf16/fp16); TX x TY threads;
 // P: planes every level advances per step (rows in 2D; 1 in 3D).
 template <int D, int R, int T, int VY, int ES, int TX, int TY, int P = 1> struct Geo {
-    static_assert(P == 1 || (P == 2 && D == 2), "two planes per step are a 2D schedule");
+    static_assert(P == 1 || ((P == 2 || P == 4) && D == 2), "several planes per step are a 2D schedule");
     static constexpr bool F32S = ES == 4;
     static constexpr int NV = cdiv(R, 4);              // 4-cell vectors of x neighbours per side
     static constexpr int ALIGN = 16 / ES;              // cells per 16 bytes of storage

@@ -105,3 +105,28 @@ def test_default_schedules_use_two_rows_for_radius_2_to_4():
         s = st.Stencil(2, r, gen.coefficients(2, r))
         d = s.default_schedule((16384, 16384))
         assert (d.t, d.planes_per_step) == (t, p), r
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_four_rows_one_level_bit_exact(dt, r):
+    """t = 1 passes with four rows per step: segments of 1, 3, 6 and 97 rows (starting on
+    every row residue mod 4), a ragged grid, a remainder-free multi-pass run."""
+    nx, ny = 264, 203
+    f = make_input(2, nx, ny)
+    c = gen.coefficients(2, r)
+    s = st.Stencil(2, r, c)
+    x = to_storage(f, dt) if dt != "f32" else torch.from_numpy(f)
+    want = oracle_passes(f, 2, r, c, 3, 1, dt) if dt != "f32" else oracle.sweep_f32(f, 2, r, c, 3)
+    for seg in (1, 3, 6, 97, 0):
+        got = run_gpu(s, x, 3, kernel=st.KERNEL_STREAM, t=1, seg=seg, planes_per_step=4)
+        assert_bits_equal(got, want, f"{dt} r={r} seg={seg} four rows")
+
+
+@pytest.mark.parametrize("shape,r", [((1, 8), 1), ((3, 16), 4), ((5, 16), 2), ((9, 8), 3)])
+def test_four_rows_tiny_grids(shape, r):
+    f = gen.uniform_grid(shape, seed=16)
+    c = gen.coefficients(2, r)
+    s = st.Stencil(2, r, c)
+    got = run_gpu(s, torch.from_numpy(f), 4, kernel=st.KERNEL_STREAM, t=1, planes_per_step=4)
+    assert_bits_equal(got, oracle.sweep_f32(f, 2, r, c, 4), f"tiny {shape} r={r} four rows")
