@@ -354,16 +354,22 @@ def suite_main(args):
             s = st.Stencil(dim, r, gen.coefficients(dim, r))
             for vy in ((1,) if dim == 2 else (2, 4)):
                 for t in range(1, st.stencil_max_t(dim, r, 0, vy) + 1):
-                    sc = st.schedule(kernel=st.KERNEL_STREAM, t=t, rows_per_thread=vy)
-                    sec = _timed(lambda: s.run(x, iters, out=out, sched=sc), reps=1)
-                    g = n * iters / sec / 1e9
-                    _row(suite=args.suite, dim=dim, r=r, t=t, rows_per_thread=vy, iters=iters, grid=list(shape),
-                         gcells=round(g, 1), gflops=round(g * metrics.flop_per_cell(dim, r), 1),
-                         roofline_gcells=round(roof(dim, r, t, 4), 1), roofline_frac=round(g / roof(dim, r, t, 4), 4))
+                    for pps in ((1, 2, 4) if dim == 2 else (1,)):
+                        sc = st.schedule(kernel=st.KERNEL_STREAM, t=t, rows_per_thread=vy, planes_per_step=pps)
+                        feats = st.stencil_schedule_features(s.handle, *(shape[::-1] + ((1,) if dim == 2 else ())),
+                                                             st.STENCIL_F32, sc)
+                        if int(feats[14]) != pps:
+                            continue   # no kernel with this many rows per step at this degree
+                        sec = _timed(lambda: s.run(x, iters, out=out, sched=sc), reps=1)
+                        g = n * iters / sec / 1e9
+                        _row(suite=args.suite, dim=dim, r=r, t=t, rows_per_thread=vy, planes_per_step=pps,
+                             iters=iters, grid=list(shape), gcells=round(g, 1),
+                             gflops=round(g * metrics.flop_per_cell(dim, r), 1),
+                             roofline_gcells=round(roof(dim, r, t, 4), 1), roofline_frac=round(g / roof(dim, r, t, 4), 4))
             sec = _timed(lambda: s.run(x, iters, out=out), reps=1)
             d = s.default_schedule(shape)
             _row(suite=args.suite, dim=dim, r=r, default_t=d.t, default_rows=d.rows_per_thread,
-                 gcells_default=round(n * iters / sec / 1e9, 1))
+                 default_planes_per_step=d.planes_per_step, gcells_default=round(n * iters / sec / 1e9, 1))
         # parity on the seeded crop at the full step count (clamp at the crop's own edges)
         side = 1024 if dim == 2 else 128
         f = crop_input(side) if dim == 2 else gen.workload_grid(3, side, side, side)

@@ -1324,6 +1324,7 @@ int stencil_schedule_features(stencil_handle h, int64_t nx, int64_t ny, int64_t 
         if (sched->seg) s.seg = sched->seg;
         if (sched->threads_x) s.threads_x = sched->threads_x;
         if (sched->threads_y) s.threads_y = sched->threads_y;
+        if (sched->planes_per_step) s.planes_per_step = sched->planes_per_step;
     }
     stencil_schedule r;
     Pass ps;
