@@ -94,7 +94,8 @@ typedef struct {
     int planes_per_step; /* 2D: rows every time level advances per step of the block's loop,
                             1, 2 (t = 1..5) or 4 (t = 1): the rows of a step share one
                             barrier, one copy wait and the loop's bookkeeping; 3D: 1.  A
-                            degree compiled with one row per step only runs with one. */
+                            degree compiled with fewer rows per step runs with the next
+                            smaller count that is compiled (4 -> 2 -> 1). */
 } stencil_schedule;
 
 /* Number of features describing one (problem, schedule) pair for the cost model. */

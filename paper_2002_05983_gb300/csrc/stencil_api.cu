@@ -388,9 +388,9 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
     const int vy = D == 3 ? s.rows_per_thread : 1;
     int pps = D == 2 && s.planes_per_step ? s.planes_per_step : 1;
     const stn::KernelEntry *e = registry().find(D, R, t, vy, dtype, h->kind(), s.threads_x, D == 3 ? s.threads_y : 0, pps);
-    if (!e && pps == 2) {   // a degree compiled with one row per step only (e.g. a remainder pass)
-        pps = 1;
-        e = registry().find(D, R, t, vy, dtype, h->kind(), s.threads_x, 0, 1);
+    while (!e && pps > 1) {   // a degree compiled with fewer rows per step (e.g. a remainder pass)
+        pps /= 2;
+        e = registry().find(D, R, t, vy, dtype, h->kind(), s.threads_x, 0, pps);
     }
     if (!e) return STENCIL_ERR_UNSUPPORTED;
     if (s.prefetch && s.prefetch != e->pf) return STENCIL_ERR_UNSUPPORTED;
