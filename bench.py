@@ -356,9 +356,12 @@ def suite_main(args):
                 for t in range(1, st.stencil_max_t(dim, r, 0, vy) + 1):
                     for pps in ((1, 2, 4) if dim == 2 else (1,)):
                         sc = st.schedule(kernel=st.KERNEL_STREAM, t=t, rows_per_thread=vy, planes_per_step=pps)
-                        feats = st.stencil_schedule_features(s.handle, *(shape[::-1] + ((1,) if dim == 2 else ())),
-                                                             st.STENCIL_F32, sc)
-                        if int(feats[14]) != pps:
+                        try:
+                            res = st.stencil_resolve_schedule(s.handle, *(shape[::-1] + ((1,) if dim == 2 else ())),
+                                                              st.STENCIL_F32, sc)
+                        except st.StencilError:
+                            continue
+                        if res.planes_per_step != pps:
                             continue   # no kernel with this many rows per step at this degree
                         sec = _timed(lambda: s.run(x, iters, out=out, sched=sc), reps=1)
                         g = n * iters / sec / 1e9

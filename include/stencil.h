@@ -208,6 +208,15 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
                  stencil_model_handle model, int store, stencil_schedule *chosen,
                  stencil_timing *rows, int cap, int *nrows);
 
+/* The fully resolved streaming schedule of one pass of degree t (sched->t, else the
+ * default's) that stencil_run_ex would launch for this problem with `sched` (NULL or
+ * partial: 0 fields = library choice): compiled block shape, segment length, prefetch
+ * depth and the rows per step actually compiled for that degree.  No device work.
+ * Errors: INVALID_ARG, UNSUPPORTED (no streaming kernel for this schedule or rows not
+ * 16-byte aligned). */
+int stencil_resolve_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                             const stencil_schedule *sched, stencil_schedule *out);
+
 /* Features of (problem, schedule) for the cost model: dim, radius, log2 nx,
  * log2 ny, log2 nz, bytes per element, t, resident warps per SM, tile height
  * (rows, 1 in 2D), log2 of the unrolled loop body's FMA count (queue period x

@@ -32,7 +32,7 @@ KERNEL_AUTO, KERNEL_STREAM, KERNEL_NAIVE = 0, 1, 2
 EXPORTS = ("stencil_create", "stencil_create_shared", "stencil_destroy", "stencil_run", "stencil_run_ex", "stencil_run_host",
            "stencil_default_schedule", "stencil_max_t", "stencil_get_device_status",
            "stencil_set_fault_injection", "stencil_set_checked", "stencil_run_noalloc", "stencil_run_batched", "stencil_tune",
-           "stencil_schedule_features", "stencil_model_create", "stencil_model_destroy",
+           "stencil_resolve_schedule", "stencil_schedule_features", "stencil_model_create", "stencil_model_destroy",
            "stencil_model_train", "stencil_model_predict", "stencil_model_normalization",
            "stencil_model_params", "stencil_model_grad", "stencil_use_cost_model", "stencil_measure_peaks", "stencil_last_cuda_error",
            "stencil_strerror")
@@ -107,6 +107,7 @@ def _lib():
                 lib.stencil_tune.argtypes = [vp, i64, i64, i64, i32, i32, vp, i32, sp,
                                              ctypes.POINTER(Timing), i32, ctypes.POINTER(i32)]
                 lib.stencil_schedule_features.argtypes = [vp, i64, i64, i64, i32, sp, fp]
+                lib.stencil_resolve_schedule.argtypes = [vp, i64, i64, i64, i32, sp, sp]
                 lib.stencil_model_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32]
                 lib.stencil_model_destroy.argtypes = [vp]
                 lib.stencil_model_train.argtypes = [vp, fp, fp, i32, i32, ctypes.c_float, fp]
@@ -231,6 +232,14 @@ def stencil_tune(h, nx, ny, nz, dtype, mode, model=None, store=True, cap=256):
     _check(_lib().stencil_tune(h, nx, ny, nz, dtype, mode, model, 1 if store else 0, ctypes.byref(chosen),
                                rows, cap, ctypes.byref(n)), "stencil_tune")
     return chosen, [rows[i] for i in range(min(n.value, cap))]
+
+
+def stencil_resolve_schedule(h, nx, ny, nz, dtype, sched: Schedule | None = None) -> Schedule:
+    """The schedule a pass would run with (block shape, segment, prefetch, rows per step)."""
+    out = Schedule()
+    _check(_lib().stencil_resolve_schedule(h, nx, ny, nz, dtype, ctypes.byref(sched) if sched is not None else None,
+                                           ctypes.byref(out)), "stencil_resolve_schedule")
+    return out
 
 
 def stencil_schedule_features(h, nx, ny, nz, dtype, sched: Schedule | None = None):

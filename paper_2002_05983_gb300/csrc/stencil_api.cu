@@ -1308,6 +1308,31 @@ int stencil_run_batched(const stencil_batch_item *items, int n, void *stream)
     return STENCIL_OK;
 }
 
+int stencil_resolve_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
+                             const stencil_schedule *sched, stencil_schedule *out)
+{
+    if (!h || !out || nx <= 0 || ny <= 0 || nz <= 0 || (h->dim == 2 && nz != 1) || dtype < STENCIL_F32 ||
+        dtype > STENCIL_F16)
+        return STENCIL_ERR_INVALID_ARG;
+    DevInfo *dev = nullptr;
+    int rc = device_info(&dev);
+    if (rc) return rc;
+    stencil_schedule s;
+    chosen_schedule(h, nx, ny, nz, dtype, &s);
+    if (sched) {
+        if (sched->t) s.t = sched->t;
+        if (sched->rows_per_thread) s.rows_per_thread = sched->rows_per_thread;
+        if (sched->seg) s.seg = sched->seg;
+        if (sched->threads_x) s.threads_x = sched->threads_x;
+        if (sched->threads_y) s.threads_y = sched->threads_y;
+        if (sched->planes_per_step) s.planes_per_step = sched->planes_per_step;
+        if (sched->prefetch) s.prefetch = sched->prefetch;
+    }
+    if (!stream_applicable(dtype, nx) || s.t < 1) return STENCIL_ERR_UNSUPPORTED;
+    Pass ps;
+    return resolve(h, nx, ny, nz, dtype, s, *dev, *out, ps);
+}
+
 int stencil_schedule_features(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
                               const stencil_schedule *sched, float *features)
 {

@@ -184,3 +184,4 @@ def test_fault_injection_times_out_and_context_survives():
     st.stencil_set_fault_injection(s.handle, -1, 0)
     got = run_gpu(s, x.cpu(), 3, kernel=st.KERNEL_STREAM, t=3)
     assert_bits_equal(got, oracle.sweep_f32(f, 2, 1, c, 3), "after fault")
+

@@ -130,3 +130,17 @@ def test_four_rows_tiny_grids(shape, r):
     s = st.Stencil(2, r, c)
     got = run_gpu(s, torch.from_numpy(f), 4, kernel=st.KERNEL_STREAM, t=1, planes_per_step=4)
     assert_bits_equal(got, oracle.sweep_f32(f, 2, r, c, 4), f"tiny {shape} r={r} four rows")
+
+
+def test_resolved_rows_per_step_fall_back_to_compiled_counts():
+    """A pass runs with the requested rows per step where that count is compiled for its
+    degree, else with the next smaller compiled count (4 -> 2 -> 1)."""
+    n = 1024
+    for r, t, asked, want in ((4, 1, 4, 4), (4, 2, 4, 2), (4, 2, 2, 2), (1, 7, 2, 1), (1, 3, 4, 2), (2, 6, 2, 1)):
+        s = st.Stencil(2, r, gen.coefficients(2, r))
+        res = st.stencil_resolve_schedule(s.handle, n, n, 1, st.STENCIL_F32,
+                                          st.schedule(kernel=st.KERNEL_STREAM, t=t, planes_per_step=asked))
+        assert (res.t, res.planes_per_step) == (t, want), (r, t, asked)
+        feats = st.stencil_schedule_features(s.handle, n, n, 1, st.STENCIL_F32,
+                                             st.schedule(kernel=st.KERNEL_STREAM, t=t, planes_per_step=asked))
+        assert int(feats[14]) == want
