@@ -90,7 +90,9 @@ typedef struct {
     int threads_y;       /* 0, or the compiled block height (3D 8) */
     int rows_per_thread; /* 3D: 2 or 4 */
     int seg;             /* stream-axis rows/planes per block, >= 1 */
-    int prefetch;        /* 0, or the compiled number of planes loaded ahead */
+    int prefetch;        /* 0, or the compiled number of planes loaded ahead by the kernel
+                            of degree t (a remainder pass of another degree runs with
+                            its own kernel's depth) */
     int planes_per_step; /* 2D: rows every time level advances per step of the block's loop,
                             1, 2 (t = 1..5) or 4 (t = 1): the rows of a step share one
                             barrier, one copy wait and the loop's bookkeeping; 3D: 1.  A

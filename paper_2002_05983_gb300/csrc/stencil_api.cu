@@ -393,7 +393,9 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
         e = registry().find(D, R, t, vy, dtype, h->kind(), s.threads_x, 0, pps);
     }
     if (!e) return STENCIL_ERR_UNSUPPORTED;
-    if (s.prefetch && s.prefetch != e->pf) return STENCIL_ERR_UNSUPPORTED;
+    // the prefetch depth is a property of the degree-t kernel; a pass of another degree (the
+    // remainder, or fewer iterations than t) runs its own kernel's
+    if (s.prefetch && t == s.t && s.prefetch != e->pf) return STENCIL_ERR_UNSUPPORTED;
     if (e->smem > static_cast<size_t>(dev.max_smem)) return STENCIL_ERR_UNSUPPORTED;
     int regs = 0;
     int rc = prepare_fn(e->fn, dev.max_smem, &regs);

@@ -16,6 +16,12 @@ constexpr unsigned kStatusBounds = 2u;   // a bounds-checked kernel found an acc
 // kChunkFma (see Geo::U).
 constexpr int kRotMaxFma = 600;
 constexpr int kChunkFma = 300;
+// Steps loaded ahead by 3D radius-1 kernels of T levels with ES-byte storage.  FP32 rings
+// of 64x16-cell tiles: t = 2 with 3 steps ahead (43.0 KB) keeps 5 blocks per SM instead
+// of 4 (+9 % on 512^3), t >= 3 with 2 steps ahead keeps 4 instead of 3 (+6 %); one level
+// keeps 4 steps (it is not limited by shared memory, and shorter steps need the
+// deeper prefetch).  16-bit input rings are small enough at 4 steps.
+__host__ __device__ constexpr int pf3r1(int t, int es) { return es != 4 || t <= 1 ? 4 : (t == 2 ? 3 : 2); }
 
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr int rup(int a, int b) { return cdiv(a, b) * b; }
@@ -67,7 +73,13 @@ template <int D, int R, int T, int VY, int ES, int TX, int TY, int P = 1> struct
     // Input ring in steps of P planes: the step that level 1 reads in shared memory lags
     // the newest by KS = ceil(L1 / P) steps; PFS steps are loaded ahead.
     static constexpr int KS = cdiv(L1, P);
-    static constexpr int DS = U * cdiv(KS + 1 + cdiv(PFMIN, P), U);   // step slots (chunk multiple)
+    // Step slots of the ring.  3D radius 1 keeps a rotating chunk of U = 3 steps, and a
+    // ring rounded up to whole chunks would hold 6 slots; its ring holds KS + 1 + pf3r1
+    // slots instead and, where that is not a chunk multiple, wraps inside a chunk
+    // (run-time slot index per step, WRAP).
+    static constexpr int DS = (D == 3 && ROT && R == 1) ? KS + 1 + pf3r1(T, ES)
+                                                        : U * cdiv(KS + 1 + cdiv(PFMIN, P), U);
+    static constexpr bool WRAP = DS % U != 0;
     static constexpr int PFS = DS - KS - 1;            // steps loaded ahead of use
     static constexpr int PF = P * PFS;                 // planes loaded ahead of use
     static constexpr int DEPTH = P * DS;               // input ring slots (planes)
@@ -75,7 +87,7 @@ template <int D, int R, int T, int VY, int ES, int TX, int TY, int P = 1> struct
     static constexpr size_t SMEM = static_cast<size_t>(kSmemHeader) +
                                    static_cast<size_t>(DEPTH) * SLOTIN * ES +
                                    static_cast<size_t>(NRING) * QP * SLOT32 * 4;
-    static constexpr bool OK = CX >= 8 && CY >= 1 && DS <= kMaxDepthIn &&
+    static constexpr bool OK = CX >= 8 && CY >= 1 && DS <= kMaxDepthIn && U <= DS &&
                                (D == 2 || (PWIN <= 256 && PH <= 256));
     // plane lag of level s (plane p of level s is handled at step (p + lag(s)) / P)
     __host__ __device__ static constexpr int lag(int s) { return s == 0 ? 0 : L1 + (s - 1) * GAP; }

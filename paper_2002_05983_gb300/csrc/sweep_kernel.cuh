@@ -440,6 +440,8 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     constexpr int QP = G::QP;
     constexpr int U = G::U, NQ = G::NQ;
     constexpr bool ROT = G::ROT;
+    constexpr bool WRAP = G::WRAP;   // input ring wraps inside a chunk (3D radius 1, P = 1)
+    static_assert(!WRAP || P == 1, "wrapping ring: one plane per step");
     constexpr bool F32S = G::F32S;
     constexpr int PADIN = G::PADIN;
     constexpr int K2 = 2 * D;
@@ -530,6 +532,12 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     const int vb = a.ny - 1 - (gy0 + yl0);             // own row index of global y = ny-1
     const bool top_cross = (D == 3) && VY > 1 && vz > 0 && vz < VY;
     const bool bot_cross = (D == 3) && VY > 1 && vb >= 0 && vb < VY - 1;
+    // block-uniform: the thread region reaches past the grid's top or bottom edge (only such
+    // tiles have threads whose rows cross it).  Radius 1 and 4 skip the clamp in other tiles
+    // with a branch (+2 % and +1 % on 512^3 against the branch-free selects); radius 2
+    // and 3 keep the selects (the branch splits the step's straight-line code: -5 % at r = 3).
+    constexpr bool YBR = R == 1 || R == 4;
+    const bool ytile = (D == 3) && VY > 1 && (!YBR || gy0 < 0 || gy0 + G::BY > a.ny);
     auto clamp_rows = [&](float (&v)[VY][4]) {
         if (top_cross) {
 #pragma unroll
@@ -669,6 +677,11 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     int kb_mod = kb % DS;       // step slot of step kb
     int lap = kb / DS;
     uint32_t bar0 = 0, par = 0;
+    const uint32_t bars_a = smem_addr(bars);
+    (void)bars_a;
+    // WRAP: step slot of step kb + J (a chunk wraps past the ring's end at most once)
+    auto wslot = [&](int J) { return kb_mod + J >= DS ? kb_mod + J - DS : kb_mod + J; };
+    (void)wslot;
     const S *inb = nullptr;     // own cell 0 in the input slot of plane P*kb
     const S *inbp = nullptr;    // ROT: own cell 0 in the input slot of plane P*kb - QP
     S *inslot = nullptr;        // input slot of plane P*kb
@@ -722,7 +735,11 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         const S *own_in = nullptr;
         const float *own32 = nullptr;
         if constexpr (s == 1) {
-            if constexpr (ROT) {
+            if constexpr (WRAP) {
+                int d = wslot(J) - G::L1;               // input slot of plane k - L1
+                d = d < 0 ? d + DS : d;
+                own_in = ring_in + d * SLOTIN + toffin;
+            } else if constexpr (ROT) {
                 constexpr int d = P * J - G::L1 + j;    // input slot of plane p relative to plane P*kb
                 own_in = d >= 0 ? inb + d * SLOTIN : inbp + (d + QP) * SLOTIN;
             } else {
@@ -826,7 +843,10 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                 res[vy][v] = acc;
             }
         }
-        if constexpr (D == 3 && VY > 1) clamp_rows(res);
+        // the last level's out-of-grid rows are neither stored nor read
+        if constexpr (D == 3 && VY > 1 && s < T) {
+            if (ytile) clamp_rows(res);
+        }
         if constexpr (s == T) {
             if (xstore) {
                 S *o = gout + static_cast<int64_t>(p) * pstride;
@@ -874,7 +894,10 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         }
         // the step's planes inside the grid were loaded together: one wait
         if (!CK || P * k <= last) {
-            if (!mbar_wait_bounded(bar0 + 8 * J, par, a.timeout_ms)) {
+            const bool ok = WRAP ? mbar_wait_bounded(bars_a + 8 * wslot(J), par ^ static_cast<uint32_t>(kb_mod + J >= DS),
+                                                     a.timeout_ms)
+                                 : mbar_wait_bounded(bar0 + 8 * J, par, a.timeout_ms);
+            if (!ok) {
                 *sflag = 1;
                 atomicOr(a.status, kStatusTimeout);
                 return;
@@ -895,14 +918,17 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                     return;
                 }
             }
-            const S *src = inb + (P * J + j) * SLOTIN;
+            S *const slot = WRAP ? ring_in + wslot(J) * SLOTIN : inslot + (P * J + j) * SLOTIN;
+            const S *src = slot + toffin;
             float v4[VY][4];
 #pragma unroll
             for (int vy = 0; vy < VY; ++vy) {
                 if (smem_ok(src + vy * PWIN, 4 * sizeof(S))) Fmt<S>::load4(src + vy * PWIN, v4[vy]);
                 else v4[vy][0] = v4[vy][1] = v4[vy][2] = v4[vy][3] = 0.f;
             }
-            if constexpr (D == 3 && VY > 1) clamp_rows(v4);
+            if constexpr (D == 3 && VY > 1) {
+                if (ytile) clamp_rows(v4);
+            }
 #pragma unroll
             for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
@@ -920,9 +946,9 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
             // the input slot is level 0's ring: clamp its out-of-grid frame now (read from the
             // next step on)
             if (gh_on) {
-                if constexpr (X4) ghost_fill_x4<sizeof(S)>(inslot + (P * J + j) * SLOTIN, gxin, PWIN, ox_in, a.nx, tid, NTHR);
-                else if constexpr (SAME) ghost_apply<sizeof(S)>(inslot + (P * J + j) * SLOTIN, gp32);
-                else ghost_apply<sizeof(S)>(inslot + (P * J + j) * SLOTIN, gpin);
+                if constexpr (X4) ghost_fill_x4<sizeof(S)>(slot, gxin, PWIN, ox_in, a.nx, tid, NTHR);
+                else if constexpr (SAME) ghost_apply<sizeof(S)>(slot, gp32);
+                else ghost_apply<sizeof(S)>(slot, gpin);
             }
         });
     };
@@ -974,7 +1000,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         bar0 = smem_addr(bars + kb_mod);
         inslot = ring_in + kb_mod * P * SLOTIN;
         inb = inslot + toffin;
-        if constexpr (ROT) inbp = ring_in + (kb_mod == 0 ? DEPTH - QP : P * kb_mod - QP) * SLOTIN + toffin;
+        if constexpr (ROT && !WRAP) inbp = ring_in + (kb_mod == 0 ? DEPTH - QP : P * kb_mod - QP) * SLOTIN + toffin;
         if (kb >= kA && kb + U - 1 <= kB) {
             SFor<0, U>::run([&](auto Jc) { step(Jc, std::false_type{}); });
         } else {
@@ -994,8 +1020,8 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
             for (int s = 1; s <= T; ++s) rb[s] = rb[s] + U >= QP ? rb[s] + U - QP : rb[s] + U;
         }
         kb_mod += U;
-        if (kb_mod == DS) {
-            kb_mod = 0;
+        if (kb_mod >= DS) {
+            kb_mod -= DS;
             ++lap;
         }
     }

@@ -72,6 +72,22 @@ def test_3d_stream_bit_exact(r, t, vy):
     assert_bits_equal(got, want, f"3D r={r} t={t} vy={vy}")
 
 
+@pytest.mark.parametrize("t", [1, 2, 3, 4])
+@pytest.mark.parametrize("seg", [7, 19, 0])
+def test_3d_r1_ring_phases(t, seg):
+    """3D radius 1 at every degree whose input ring is not a whole number of chunks
+    (t = 2: 5 slots, t = 3: 4 slots, chunks of 3 steps) and its neighbours: segments of 7
+    and 19 planes start the blocks at every offset in the ring and the chunk, so each
+    slot is reused in both phases of its mbarrier on several laps."""
+    nx, ny, nz = 100, 70, 53
+    c = gen.coefficients(3, 1)
+    f = make_input(3, nx, ny, nz)
+    iters = 2 * t + 1
+    s = st.Stencil(3, 1, c)
+    got = run_gpu(s, torch.from_numpy(f), iters, kernel=st.KERNEL_STREAM, t=t, rows_per_thread=2, seg=seg)
+    assert_bits_equal(got, oracle.sweep_f32(f, 3, 1, c, iters), f"3D r=1 t={t} seg={seg}")
+
+
 @pytest.mark.parametrize("dim,r", [(2, 1), (2, 4), (2, 6), (3, 1), (3, 3), (3, 5)])
 def test_schedules_bit_identical_to_naive(dim, r):
     """Every FP32 schedule equals the one-thread-per-cell t=1 schedule bit for bit."""
@@ -169,19 +185,26 @@ def test_run_host_end_to_end():
     assert_bits_equal(out, oracle.sweep_f32(f, 3, 2, c, 6), "run_host")
 
 
-def test_fault_injection_times_out_and_context_survives():
+@pytest.mark.parametrize("dim,shape,r,t", [
+    (2, (64, 128), 1, 3),
+    (3, (24, 40, 72), 1, 2),    # input ring of 5 slots that wraps inside a 3-step chunk
+    (3, (24, 40, 72), 1, 3),    # 4 slots
+    (3, (24, 40, 72), 4, 1),    # shifting queue
+])
+def test_fault_injection_times_out_and_context_survives(dim, shape, r, t):
     """A copy that is never issued makes the bounded wait expire: the kernel records
-    TIMEOUT and returns; the same context keeps working afterwards."""
-    f = gen.uniform_grid((64, 128), seed=8)
-    c = gen.coefficients(2, 1)
-    s = st.Stencil(2, 1, c)
+    TIMEOUT, lets its copies in flight land and returns; the same context keeps working
+    afterwards."""
+    f = gen.uniform_grid(shape, seed=8)
+    c = gen.coefficients(dim, r)
+    s = st.Stencil(dim, r, c)
     x = torch.from_numpy(f).cuda()
     assert st.stencil_get_device_status(clear=True) == 0
     st.stencil_set_fault_injection(s.handle, 10, 50)
-    s.run(x, 3, sched=st.schedule(kernel=st.KERNEL_STREAM, t=3))
+    s.run(x, t, sched=st.schedule(kernel=st.KERNEL_STREAM, t=t))
     assert st.stencil_get_device_status(clear=True) == st.STENCIL_ERR_TIMEOUT
     assert st.stencil_get_device_status() == 0
     st.stencil_set_fault_injection(s.handle, -1, 0)
-    got = run_gpu(s, x.cpu(), 3, kernel=st.KERNEL_STREAM, t=3)
-    assert_bits_equal(got, oracle.sweep_f32(f, 2, 1, c, 3), "after fault")
+    got = run_gpu(s, x.cpu(), t, kernel=st.KERNEL_STREAM, t=t)
+    assert_bits_equal(got, oracle.sweep_f32(f, dim, r, c, t), f"after fault {dim}D r={r} t={t}")
 
