@@ -281,12 +281,13 @@ def case_main(args):
     f = args.case.split(":")
     dim, r, t, n, iters = (int(v) for v in f[:5])
     dt = f[5] if len(f) > 5 else "f32"
+    pps = int(f[6]) if len(f) > 6 else 0          # 2D rows per step (0: the library's choice)
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dt]
     shape = (n, n) if dim == 2 else (n, n, n)
     x = torch.from_numpy(gen.workload_grid(dim, *shape[::-1])).to(tdt).cuda()
     out = torch.empty_like(x)
     s = st.Stencil(dim, r, gen.coefficients(dim, r))
-    sched = st.schedule(kernel=st.KERNEL_STREAM, t=t) if t else None
+    sched = st.schedule(kernel=st.KERNEL_STREAM, t=t, planes_per_step=pps) if t else None
     for _ in range(args.warmup):
         s.run(x, iters, out=out, sched=sched)
     torch.cuda.synchronize()
@@ -726,7 +727,7 @@ def main():
     ap.add_argument("--model-accuracy", action="store_true",
                     help="analytic model vs measurement on the benchmark configurations (Table III form)")
     ap.add_argument("--case", default=None,
-                    help="single sweep for profiling: dim:r:t:n:iters[:dtype] (grid n^dim, t=0 auto)")
+                    help="single sweep for profiling: dim:r:t:n:iters[:dtype[:rows_per_step]] (grid n^dim, t=0 auto)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)

@@ -164,10 +164,13 @@ template <> struct Fmt<__nv_bfloat16> {
     static constexpr int pad = 8;
     __device__ __forceinline__ static void load4(const __nv_bfloat16 *p, float (&v)[4])
     {
+        // a BF16 value is the upper half of the binary32 with the same bits: the lower cell of
+        // each 32-bit pair moves up by 16 bits, the upper one keeps its place (exact)
         const uint2 t = *reinterpret_cast<const uint2 *>(p);
-        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.x));
-        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.y));
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        v[0] = __uint_as_float(t.x << 16);
+        v[1] = __uint_as_float(t.x & 0xffff0000u);
+        v[2] = __uint_as_float(t.y << 16);
+        v[3] = __uint_as_float(t.y & 0xffff0000u);
     }
     __device__ __forceinline__ static void store4(__nv_bfloat16 *p, const float (&v)[4])
     {
