@@ -34,11 +34,15 @@ template <int D, int R, int T, int VY, int ES, int TX, int TY, int P = 1> struct
     static constexpr bool F32S = ES == 4;
     static constexpr int NV = cdiv(R, 4);              // 4-cell vectors of x neighbours per side
     static constexpr int ALIGN = 16 / ES;              // cells per 16 bytes of storage
-    static constexpr int PADIN = ALIGN > 4 * NV ? ALIGN : 4 * NV;   // input row padding (cells)
     static constexpr int PAD32 = 4 * NV;               // FP32 ring row padding (cells)
     static constexpr int BX = 4 * TX;                  // thread-region width (cells)
     static constexpr int BY = (D == 3) ? TY * VY : 1;  // thread-region rows (3D)
-    static constexpr int HTX = rup((T - 1) * R, ALIGN);   // x halo of levels 1..T (16-byte multiple)
+    // x halo of levels 1..T in whole 4-cell vectors.  Tile origins (multiples of CX) and the
+    // input box origin gx0 - PADIN stay on 16-byte boundaries: CX = BX - 2*HTX is a multiple of
+    // 8 cells, and the input padding (at least the 4*NV cells the neighbour loads reach) takes
+    // 4 more cells where HTX + 4*NV is not a 16-byte multiple (16-bit storage only).
+    static constexpr int HTX = rup((T - 1) * R, 4);
+    static constexpr int PADIN = (HTX + 4 * NV) % ALIGN == 0 ? 4 * NV : 4 * NV + 4;   // input row padding
     static constexpr int HTY = (D == 3) ? (T - 1) * R : 0;
     static constexpr int CX = BX - 2 * HTX;            // compute tile (Eq. 2: bsize - 2 t r)
     static constexpr int CY = (D == 3) ? BY - 2 * HTY : 1;
@@ -87,6 +91,7 @@ template <int D, int R, int T, int VY, int ES, int TX, int TY, int P = 1> struct
     static constexpr size_t SMEM = static_cast<size_t>(kSmemHeader) +
                                    static_cast<size_t>(DEPTH) * SLOTIN * ES +
                                    static_cast<size_t>(NRING) * QP * SLOT32 * 4;
+    static_assert(BX % ALIGN == 0 && CX % ALIGN == 0 && (HTX + PADIN) % ALIGN == 0, "16-byte tile and box origins");
     static constexpr bool OK = CX >= 8 && CY >= 1 && DS <= kMaxDepthIn && U <= DS &&
                                (D == 2 || (PWIN <= 256 && PH <= 256));
     // plane lag of level s (plane p of level s is handled at step (p + lag(s)) / P)
