@@ -217,6 +217,32 @@ def traffic_for(dim, r, t, dtype="f32"):
     return None
 
 
+def limiter_for(dim, r, t, hbm_frac, dtype="f32"):
+    """What limits a kernel: ncu's DRAM / FMA-pipe / issue figures from the committed summary (while
+    the kernel sources keep that hash) and the live fraction of the HBM roof.  "hbm" when the live
+    bandwidth is >= 85 % of the measured copy peak or ncu shows DRAM >= 80 %, "alu" when the FMA pipe
+    is >= 80 % busy, else "issue" (neither unit saturated: the issue rate and latencies set the speed)."""
+    path = os.path.join(ROOT, "profiles", "ncu_limits.txt")
+    csrc = os.path.join(ROOT, "paper_2002_05983_gb300", "csrc")
+    out = {"hbm_frac_live": round(hbm_frac, 4) if hbm_frac is not None else None}
+    if os.path.exists(path):
+        h = kernel_source_hash(csrc)
+        for ln in open(path):
+            f = ln.split()
+            if len(f) == 10 and not ln.startswith("#") and f[0] == h and f[1:5] == [str(dim), str(r), str(t), dtype]:
+                out.update(dram_pct=float(f[5]), fma_pipe_pct=float(f[6]), issue_per_scheduler=float(f[7]),
+                           top_stall=f[8], source="ncu, profiles/ncu_limits.txt")
+    if (hbm_frac or 0) >= 0.85 or out.get("dram_pct", 0) >= 80:
+        out["kind"] = "hbm"
+    elif out.get("fma_pipe_pct", 0) >= 80:
+        out["kind"] = "alu"
+    elif "dram_pct" in out:
+        out["kind"] = "issue"
+    else:
+        out["kind"] = None   # no counters for this kernel source
+    return out
+
+
 def host_cpu():
     """CPU model (from /proc/cpuinfo, else the machine type) and the CPUs this process may use."""
     model = platform.machine()
@@ -553,6 +579,7 @@ def measure_3d(pk, stream):
                      "gflops": round(g * metrics.flop_per_cell(3, r), 1), "roofline_gcells": round(roof, 1),
                      "roofline_frac": round(g / roof, 4),
                      "bound": metrics.roofline_bound(3, r, d.t, 4, pk["fp32_flops"], pk["hbm_gbs"] * 1e9),
+                     "limiter": limiter_for(3, r, d.t, g * 8 / (d.t * pk["hbm_gbs"])),
                      "ms": round(sec * 1e3, 2)})
         s.close()
     assert st.stencil_get_device_status() == 0
@@ -860,6 +887,7 @@ def main():
                      "gflops": round(g * metrics.flop_per_cell(2, r), 1),
                      "roofline_gcells": round(roof, 1), "roofline_frac": round(g / roof, 4),
                      "bound": metrics.roofline_bound(2, r, t, 4, pk["fp32_flops"], pk["hbm_gbs"] * 1e9),
+                     "limiter": limiter_for(2, r, t, g * 8 / (t * pk["hbm_gbs"])),
                      "ms": round(sec * 1e3, 2)})
     dom = max(rows, key=lambda d: d["ms"])
     nl = -(-ITERS // dom["t"])
@@ -876,6 +904,8 @@ def main():
     roofline["kernel"] = f"sweep_kernel<2D, r={dom['r']}, t={dom['t']}, fp32>"
     roofline["traffic"] = traffic_for(2, dom["r"], dom["t"])
     roofline["algorithmic_bytes_per_launch"] = NX * NY * 8
+    # `bound` names the lower roof of R(t); what limits the kernel in practice, from ncu's counters
+    roofline["limiter"] = dom["limiter"]
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": "GCell/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 2),
