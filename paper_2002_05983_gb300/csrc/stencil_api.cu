@@ -806,7 +806,7 @@ std::vector<char> batch_key(const stencil_batch_item *items, int n, int dev)
         const stencil_plan *h = items[i].h;
         const char *c = reinterpret_cast<const char *>(h->c);
         k.insert(k.end(), c, c + sizeof(float) * h->K);
-        int extra[2] = {h->fault_plane, h->timeout_ms};
+        int extra[3] = {h->fault_plane, h->timeout_ms, h->kind()};   // kind: shared / checked kernels
         k.insert(k.end(), reinterpret_cast<char *>(extra), reinterpret_cast<char *>(extra) + sizeof(extra));
         stencil_schedule sc;   // the schedule the batch will use for this grid
         chosen_schedule(h, items[i].nx, items[i].ny, items[i].nz, items[i].dtype, &sc);
@@ -907,7 +907,8 @@ int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cuda
                 last_task[x->item] = static_cast<int>(tasks.size());
                 tasks.push_back(tk);
             }
-            BatchClass c;
+            E->classes.emplace_back();   // owned by E from here on: freed with it on any error below
+            BatchClass &c = E->classes.back();
             c.pfn = kind->pfn;
             c.phase = phase;
             c.block = dim3(kind->tx, kind->ty);
@@ -937,7 +938,6 @@ int build_batch(const stencil_batch_item *items, int n, const DevInfo &dev, cuda
             B.total = total;
             B.timeout_ms = timeout;
             B.fault_task = fault_task;
-            E->classes.push_back(c);
         }
     }
     // One CUDA graph.  Phase 0: every class resets its counters and runs its persistent launch
