@@ -613,14 +613,24 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     }
     __syncthreads();
 
-    // thread 0 issues the input loads: step kq brings planes P*kq + j (j < P, up to lmax)
-    // into the P slots of step slot kq mod DS, completing one mbarrier phase
+    // One thread issues the input loads of a step: step kq brings planes P*kq + j (j < P, up
+    // to lmax) into the P slots of step slot kq mod DS, completing one mbarrier phase.  Thread
+    // 0 issues the prologue's loads, and every later step's too, except in 2D kernels with
+    // 16-bit storage and several rows per step (RPROD): there the producer rotates over the
+    // block's warps (lane 0 of warp k mod NW at step k), so that no warp carries the issue
+    // work of every step into the step's barrier (measured +3 to +8 % for BF16/FP16 r = 2..4;
+    // one-row kernels lost 3 %, 2D FP32 kernels gained nothing, and 3D ones need more
+    // registers for it).  The producers' record of what was issued and waited for
+    // (issued_hi, consumed_hi) serves the drain after an abort.
+    constexpr bool RPROD = D == 2 && !F32S && P >= 2;
+    constexpr int NW = NTHR / 32;
+    static_assert(NW >= 1 && (NW & (NW - 1)) == 0, "whole warps, a power of two");
     int issued_hi = k0 - 1;
     auto issue = [&](int kq) {
         const int sslot = kq % DS;
         const uint32_t bar = smem_addr(bars + sslot);
         S *dst0 = ring_in + sslot * P * SLOTIN;
-        issued_hi = kq;
+        if constexpr (!RPROD) issued_hi = kq;
         if (a.fault_plane >= P * kq && a.fault_plane < P * kq + P) return;   // test hook: never complete
         if constexpr (D == 2) {
             const int xa = max(ox_in, 0), xb = min(ox_in + PWIN, a.nx);
@@ -657,9 +667,11 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
             tma_load_3d(smem_addr(dst0), tmap, ox_in, oy, q, bar);
         }
     };
-    if (tid == 0) {
+    {
         const int qe = min(k0 + G::PFS - 1, smax);
-        for (int kq = k0; kq <= qe; ++kq) issue(kq);
+        if (tid == 0)
+            for (int kq = k0; kq <= qe; ++kq) issue(kq);
+        if constexpr (RPROD) issued_hi = max(issued_hi, qe);   // every thread keeps the record
     }
 
     float q[T][NQ][VY][4];
@@ -672,7 +684,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
 #pragma unroll
                 for (int v = 0; v < 4; ++v) q[s][j][vy][v] = 0.f;
 
-    int consumed_hi = k0 - 1;   // last input step waited for by thread 0
+    int consumed_hi = k0 - 1;   // last input step waited for
     bool aborted = false;
 
     // per-chunk state (a chunk is U steps; kb is a multiple of U)
@@ -905,7 +917,7 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                 atomicOr(a.status, kStatusTimeout);
                 return;
             }
-            if (tid == 0) consumed_hi = k;
+            if (RPROD || tid == 0) consumed_hi = k;
         }
         SFor<0, P>::run([&](auto jc) {
             constexpr int j = decltype(jc)::value;
@@ -966,11 +978,14 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
             if (k < k0 || k > k1) return;
         }
         // keep PFS steps of input in flight
-        if (tid == 0) {
+        {
             const int kn = k + G::PFS;
             if (kn <= smax) {
-                if (gh_on) fence_proxy_async_smem();
-                issue(kn);
+                if (tid == (RPROD ? (k & (NW - 1)) << 5 : 0)) {
+                    if (gh_on) fence_proxy_async_smem();
+                    issue(kn);
+                }
+                if constexpr (RPROD) issued_hi = kn;
             }
         }
         // levels T..2 highest first, then level 0 (the input), then level 1 (reads the input ring)

@@ -185,20 +185,21 @@ def test_run_host_end_to_end():
     assert_bits_equal(out, oracle.sweep_f32(f, 3, 2, c, 6), "run_host")
 
 
-@pytest.mark.parametrize("dim,shape,r,t", [
-    (2, (64, 128), 1, 3),
-    (3, (24, 40, 72), 1, 2),    # input ring of 5 slots that wraps inside a 3-step chunk
-    (3, (24, 40, 72), 1, 3),    # 4 slots
-    (3, (24, 40, 72), 4, 1),    # shifting queue
+@pytest.mark.parametrize("dim,shape,r,t,dt", [
+    (2, (64, 128), 1, 3, "f32"),
+    (2, (96, 256), 4, 2, "bf16"),    # 16-bit 2D, two rows per step: the producer rotates over the warps
+    (3, (24, 40, 72), 1, 2, "f32"),  # input ring of 5 slots that wraps inside a 3-step chunk
+    (3, (24, 40, 72), 1, 3, "f32"),  # 4 slots
+    (3, (24, 40, 72), 4, 1, "f32"),  # shifting queue
 ])
-def test_fault_injection_times_out_and_context_survives(dim, shape, r, t):
+def test_fault_injection_times_out_and_context_survives(dim, shape, r, t, dt):
     """A copy that is never issued makes the bounded wait expire: the kernel records
     TIMEOUT, lets its copies in flight land and returns; the same context keeps working
     afterwards."""
     f = gen.uniform_grid(shape, seed=8)
     c = gen.coefficients(dim, r)
     s = st.Stencil(dim, r, c)
-    x = torch.from_numpy(f).cuda()
+    x = to_storage(f, dt).cuda() if dt != "f32" else torch.from_numpy(f).cuda()
     assert st.stencil_get_device_status(clear=True) == 0
     st.stencil_set_fault_injection(s.handle, 10, 50)
     s.run(x, t, sched=st.schedule(kernel=st.KERNEL_STREAM, t=t))
@@ -206,5 +207,6 @@ def test_fault_injection_times_out_and_context_survives(dim, shape, r, t):
     assert st.stencil_get_device_status() == 0
     st.stencil_set_fault_injection(s.handle, -1, 0)
     got = run_gpu(s, x.cpu(), t, kernel=st.KERNEL_STREAM, t=t)
-    assert_bits_equal(got, oracle.sweep_f32(f, dim, r, c, t), f"after fault {dim}D r={r} t={t}")
+    want = oracle.sweep_f32(f, dim, r, c, t) if dt == "f32" else oracle_passes(f, dim, r, c, t, t, dt)
+    assert_bits_equal(got, want, f"after fault {dim}D r={r} t={t} {dt}")
 
