@@ -191,12 +191,17 @@ int stencil_default_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t n
  *    its bookkeeping instructions, at a share of the SM issue rate that falls
  *    with the resident warps per SM; no device work.
  *  - EXHAUSTIVE: allocates an input and output grid of the problem's size
- *    (cudaMalloc), runs each candidate for >= 16 steps after a warm-up, takes
- *    the best of two CUDA-event timings, frees the grids; synchronous.
+ *    (cudaMalloc), runs each candidate after a warm-up for >= 16 steps and
+ *    >= 2^30 cell updates (at most 1000 steps: small grids get longer runs, so
+ *    launch latency does not decide the timing), takes the best of two
+ *    CUDA-event timings, frees the grids; synchronous.
  *  - MODEL: needs `model` (stencil_model_train), trained to predict
  *    log(measured / analytic time) from the features; the prediction of a
- *    candidate is its analytic time times exp(model output).  No device work
- *    besides the model's forward pass.
+ *    candidate is its analytic time times exp(model output).  The candidate
+ *    with the lowest prediction is picked if it is predicted at least 5 % faster
+ *    than the analytic model's pick, else the analytic pick (a trust region:
+ *    smaller predicted gains are within the model's fit error).  No device
+ *    work besides the model's forward pass.
  * `chosen` receives the pick; `rows` (capacity `cap`, may be NULL) receives one
  * stencil_timing per candidate and *nrows their number.  With `store` != 0 the
  * pick is kept in the handle and used by later stencil_run calls on the same

@@ -1418,9 +1418,13 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
         cudaEventCreate(&e1);
         cudaMemset(a, 0, bytes);
         int err = 0;
+        // every timing covers >= 16 steps and, for small grids, >= 2^30 cell updates (about a
+        // millisecond): shorter runs are dominated by launch latency and jitter
+        const double cells = static_cast<double>(nx) * ny * nz;
+        const int steps = static_cast<int>(std::min(1000.0, std::max(16.0, std::ceil(1073741824.0 / cells))));
         for (int i = 0; i < nc && !err; ++i) {
             const int t = tim[i].sched.t;
-            const int iters = t * std::max(2, (16 + t - 1) / t);
+            const int iters = t * std::max(2, (steps + t - 1) / t);
             err = run_impl(h, a, b, nx, ny, nz, iters, dtype, nullptr, &tim[i].sched);
             float best = 1e30f;
             for (int rep = 0; rep < 2 && !err; ++rep) {
@@ -1448,6 +1452,16 @@ int stencil_tune(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype
     };
     for (int i = 1; i < nc; ++i)
         if (key(tim[i]) < key(tim[best])) best = i;
+    if (mode == STENCIL_TUNE_MODEL) {
+        // trust region around the analytic pick: the learned correction replaces it only where
+        // it predicts at least kModelMargin less time for its own pick than for the analytic one
+        // (smaller predicted gains are within the model's fit error, log-RMS about 7 %)
+        int ia = 0;
+        for (int i = 1; i < nc; ++i)
+            if (tim[i].analytic_ns_per_cell < tim[ia].analytic_ns_per_cell) ia = i;
+        constexpr float kModelMargin = 0.05f;
+        if (!(tim[best].model_ns_per_cell < (1.f - kModelMargin) * tim[ia].model_ns_per_cell)) best = ia;
+    }
     *chosen = tim[best].sched;
     if (store) {
         bool found = false;

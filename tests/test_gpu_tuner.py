@@ -122,7 +122,11 @@ def test_tune_modes_pick_valid_schedules(dim, r, shape, dt):
     mc, mrows = st.stencil_tune(s.handle, nx, ny, nz, dt, st.TUNE_MODEL, model=m, store=False)
     assert all(t.model_ns_per_cell > 0 for t in mrows)
     pred = np.array([t.model_ns_per_cell for t in mrows])
-    assert tune.same_schedule(mc, mrows[int(np.argmin(pred))].sched)
+    # the lowest prediction, unless it is less than 5 % below the analytic pick's (trust region)
+    im = int(np.argmin(pred))
+    ia = int(np.argmin([t.analytic_ns_per_cell for t in mrows]))
+    want = im if pred[im] < (1 - 0.05) * pred[ia] else ia
+    assert tune.same_schedule(mc, mrows[want].sched)
     np.testing.assert_allclose(pred, [t.analytic_ns_per_cell for t in mrows] *
                                np.exp(st.stencil_model_predict(m, X)), rtol=1e-5)
     st.stencil_model_destroy(m)
