@@ -234,7 +234,11 @@ void default_schedule(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz,
         d.planes_per_step = h->r >= 2 && reg.find(2, h->r, d.t, 1, dtype, h->kind(), 128, 0, 2) ? 2 : 1;
     } else {
         d.t = h->r == 1 ? 2 : 1;
-        d.rows_per_thread = 2;
+        // FP32 radius 3 and 4 (one level, packed two-lane arithmetic): 4 rows per thread
+        // measured 670 / 613 against 654 / 591 GCell/s with 2 rows on 512^3
+        const bool four = dtype == STENCIL_F32 && h->kind() == 0 && d.t == 1 && (h->r == 3 || h->r == 4) &&
+                          reg.find(3, h->r, 1, 4, dtype, 0, 16, 8, 1) != nullptr;
+        d.rows_per_thread = four ? 4 : 2;
         d.threads_x = 16;
         d.threads_y = 8;
         d.planes_per_step = 1;
@@ -463,6 +467,7 @@ int plan_pass(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, int dty
     a.fault_plane = h->fault_plane;
     a.status = dev.status;
     std::memcpy(a.c, h->c, sizeof(float) * h->K);
+    for (int k = 0; k < h->K; ++k) a.cc[2 * k] = a.cc[2 * k + 1] = h->c[k];
     return 0;
 }
 

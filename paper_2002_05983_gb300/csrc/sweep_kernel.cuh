@@ -60,6 +60,7 @@ struct SweepArgs {
     int timeout_ms;       // limit of every bounded wait
     int fault_plane;      // test hook: never load this input plane (< 0: off)
     float c[kMaxK];       // coefficients, Eq. 1 order
+    alignas(8) float cc[2 * kMaxK];   // each coefficient twice: the operand pairs of the packed two-lane FMAs
 };
 
 // --------------------------------------------------------------- PTX helpers
@@ -144,6 +145,32 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
+}
+
+// Packed two-lane FP32 arithmetic (sm_100 and later): two cells' chains advance in one
+// instruction, each lane an IEEE multiply or fused multiply-add of its own, so a cell's
+// value is the same as with scalar instructions in the same order.
+__device__ __forceinline__ uint64_t pk2(float a, float b)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(uint64_t r, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
 
 // --------------------------------------------------------- storage formats
@@ -485,6 +512,16 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
     // for r >= 2; 3D kernels, tighter on registers, gain nothing and keep the default).
     // SH: one coefficient per distance, c[0] centre and c[i] for distance i.
     constexpr int K = SH ? 1 + R : 1 + 2 * D * R;
+    // Packed two-lane FP32 arithmetic (cells 0,1 and 2,3 of a row in lockstep; bit-identical
+    // to the scalar chain) where it measured faster: 3D FP32 one-level passes of radius 3
+    // (+3 %, coefficient pairs read from the kernel parameters) and 4 (+1.3 %, pairs held in
+    // registers).  Elsewhere its 30-40 extra registers cost more than the issue slots it saves.
+    constexpr bool PK = !SH && D == 3 && T == 1 && F32S && (R == 3 || R == 4);
+    constexpr bool PKC = R == 3;   // coefficient pairs from the parameters (else registers)
+    auto cpair = [&](int k) -> uint64_t {   // coefficient k in both lanes
+        if constexpr (PKC) return *reinterpret_cast<const uint64_t *>(&a.cc[2 * k]);
+        else return 0;
+    };
     float cf[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
@@ -786,6 +823,17 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
         }
         constexpr int NV = G::NV;
         float res[VY][4];
+        uint64_t cpr[PK && !PKC ? K : 1];   // coefficient pairs held in registers
+        (void)cpr;
+        if constexpr (PK && !PKC) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) cpr[i] = pk2(cf[i], cf[i]);
+        }
+        auto cp = [&](int k) -> uint64_t {
+            if constexpr (PK && !PKC) return cpr[k];
+            else return cpair(k);
+        };
+        (void)cp;
 #pragma unroll
         for (int vy = 0; vy < VY; ++vy) {
             // L[m] holds cells x0-4(m+1) .. x0-4m-1, Rr[m] cells x0+4(m+1) .. x0+4m+7
@@ -816,6 +864,48 @@ __device__ __forceinline__ bool sweep_tile(const CUtensorMap *tmap, const SweepA
                 }
             }
             const float(&ctr)[VY][4] = q[s - 1][jcq];
+            if constexpr (PK) {
+                // cell v + d of this row (|d| <= 4*NV): own vector, or the left/right neighbour vectors
+                auto nb = [&](int v, int d) -> float {
+                    const int x = v + d;
+                    if (x >= 0 && x <= 3) return ctr[vy][cclamp(x, 0, 3)];
+                    if (x < 0) return L[cclamp((-x - 1) / 4, 0, NV - 1)][cclamp(x + 4 * ((-x - 1) / 4 + 1), 0, 3)];
+                    return Rr[cclamp(x / 4 - 1, 0, NV - 1)][cclamp(x % 4, 0, 3)];
+                };
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int v = 2 * h;   // cells v and v + 1 in the two lanes
+                    uint64_t acc = mul2(cp(0), pk2(ctr[vy][v], ctr[vy][v + 1]));
+#pragma unroll
+                    for (int i = 1; i <= R; ++i) {
+                        const int cb = 1 + (i - 1) * K2;
+                        if ((i & 1) == 0) {   // even distance: both x neighbours are register pairs too
+                            acc = fma2(cp(cb + 0), pk2(nb(v, -i), nb(v + 1, -i)), acc);
+                            acc = fma2(cp(cb + 1), pk2(nb(v, i), nb(v + 1, i)), acc);
+                        } else {              // odd distance: one lane at a time
+                            float a0, a1;
+                            upk2(acc, a0, a1);
+                            a0 = __fmaf_rn(cf[cb + 0], nb(v, -i), a0);
+                            a1 = __fmaf_rn(cf[cb + 0], nb(v + 1, -i), a1);
+                            a0 = __fmaf_rn(cf[cb + 1], nb(v, i), a0);
+                            a1 = __fmaf_rn(cf[cb + 1], nb(v + 1, i), a1);
+                            acc = pk2(a0, a1);
+                        }
+                        if constexpr (D == 3) {
+                            const float *sp = (vy - i >= 0) ? &ctr[cclamp(vy - i, 0, VY - 1)][0] : &up[cclamp(i - vy - 1, 0, R - 1)][0];
+                            const float *np = (vy + i < VY) ? &ctr[cclamp(vy + i, 0, VY - 1)][0] : &dn[cclamp(vy + i - VY, 0, R - 1)][0];
+                            acc = fma2(cp(cb + 2), pk2(sp[v], sp[v + 1]), acc);
+                            acc = fma2(cp(cb + 3), pk2(np[v], np[v + 1]), acc);
+                        }
+                        const float(&bq)[VY][4] = q[s - 1][qrd(s, J, j, -i)];
+                        const float(&aq)[VY][4] = q[s - 1][qrd(s, J, j, i)];
+                        acc = fma2(cp(cb + K2 - 2), pk2(bq[vy][v], bq[vy][v + 1]), acc);
+                        acc = fma2(cp(cb + K2 - 1), pk2(aq[vy][v], aq[vy][v + 1]), acc);
+                    }
+                    upk2(acc, res[vy][v], res[vy][v + 1]);
+                }
+                continue;
+            }
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 float acc = __fmul_rn(cf[0], ctr[vy][v]);
