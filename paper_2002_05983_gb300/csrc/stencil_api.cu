@@ -690,7 +690,16 @@ double analytic_ns(const stencil_plan *h, int64_t nx, int64_t ny, int64_t nz, in
     const double nblk = std::ceil(tiles * ns_axis / s.seg);
     const int P = e->p, VY = e->vy, NV = (R + 3) / 4;
     const double cells = 4.0 * VY * P;                               // per thread, level and step
-    const double fp = cells * (2.0 * D * R + 1.0);   // both coefficient forms: 2*D*r + 1 FP32 instructions
+    // FP32 instructions per cell: 2*D*r + 1 (both coefficient forms); the 3D FP32 one-level
+    // kernels of radius 3 and 4 run two cells per packed instruction except the x terms of
+    // odd distance: 1/2 for the centre, 3 per even and 4 per odd distance
+    const bool packed = D == 3 && t == 1 && dtype == STENCIL_F32 && !h->shared && (R == 3 || R == 4);
+    double fpc = 2.0 * D * R + 1.0;
+    if (packed) {
+        fpc = 0.5;
+        for (int i = 1; i <= R; ++i) fpc += (i % 2 == 0) ? 3.0 : 4.0;
+    }
+    const double fp = cells * fpc;
     const double book = (D == 2 ? 2.6 + 4.5 * R + 13.9 * P
                                 : 20.0 + 2.0 * (2.0 * R + 2.0 * NV) * VY + (e->rot ? 0.0 : 6.0 * VY * e->qp / e->u)) +
                         (es == 2 ? 10.0 * P / t : 0.0);   // level 1 of t widens its 16-bit neighbour loads
