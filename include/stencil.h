@@ -177,7 +177,7 @@ int stencil_run_host(stencil_handle h, const void *in_host, void *out_host, int6
  * with stencil_use_cost_model, else the library's rule (2D: radius 1 at t = 4
  * with one row per step, radius 2..4 at t = 3, 2, 2 with two rows per step --
  * 16-bit storage radius 3 at t = 3 --, radius 5, 6 at t = 2; 3D: t = 2 for
- * radius 1, else t = 1, 2 rows per thread). */
+ * radius 1, else t = 1; 2 rows per thread, 4 for FP32 radius 3 and 4). */
 int stencil_default_schedule(stencil_handle h, int64_t nx, int64_t ny, int64_t nz, int dtype,
                              stencil_schedule *out);
 
